@@ -1,0 +1,328 @@
+"""Benchmark of the IMPM elastomer substep on GB300.
+
+Workload: the 4,194,304-particle sensor pad (128x128x32 cells at dx =
+0.3125 mm, sphere indenter, press 1 mm / slip 3 mm / rotate 30 deg over
+20,000 substeps, 128x128 surface readout every 100 substeps).  One bench
+step = 100 IMPM substeps (every relative-rest pass of Algorithm 1 included)
+plus the surface readout of that frame.  Metric: particle-updates/s, one
+update = one particle through one P2G -> grid -> G2P pass.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank runs its own replica of the pad (independent
+instances shard with no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPM particle-updates/s (4.2M pts, FP32) & surrogate vs MPM frames/s at ≤2% err"
+UNIT = "particle-updates/s"
+SUBSTEPS_PER_STEP = 100
+BYTES_PER_UPDATE = 96          # x (12 B) + F (36 B), read once and written once per committed update
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([a.strip() for a in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, val in zip(names, r[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("tsim_kernels.cu", "tsim_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2405_02914_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(n_particles):
+    """DRAM bytes per commit launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "transfer_commit_traffic.json")) as f:
+            t = json.load(f)
+        if t.get("kernel_hash") != _kernel_hash():
+            return None
+        return float(t["dram_bytes_per_particle"]) * n_particles
+    except Exception:
+        return None
+
+
+def cpu_baseline(scene, max_seconds=15.0):
+    """The FP64 oracle as it stands, single-threaded, on the first substeps."""
+    import oracle as O
+    from paper_2405_02914_gb300 import inputs as I
+    x, tag = I.gel_particles(scene.gel)
+    v, C, F = I.rest_state(x.shape[0])
+    st = O.State(x, v, C, F, tag)
+    s, ind = O.make_scene(scene), O.make_indenter(scene.ind)
+    done, passes, t0 = 0, 0, time.perf_counter()
+    while True:
+        pl, _ = O.run(s, ind, scene.keyframes, done, 1, st)
+        done += 1
+        passes += int(pl.sum())
+        el = time.perf_counter() - t0
+        if el > max_seconds or done >= 50:
+            break
+    return {"value": x.shape[0] * passes / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d substeps (%d passes) of the 4,194,304-particle pad press, FP64 oracle, "
+                      "serial, %.1f s" % (done, passes, el)}
+
+
+def run_reference(args, scene):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2405_02914_gb300 import inputs as I
+    x, tag = I.gel_particles(scene.gel)
+    v, C, F = I.rest_state(x.shape[0])
+    st = O.State(x, v, C, F, tag)
+    s, ind = O.make_scene(scene), O.make_indenter(scene.ind)
+    k = 0
+    for _ in range(args.warmup):
+        O.run(s, ind, scene.keyframes, k, 1, st)
+        k += 1
+    passes, t0 = 0, time.perf_counter()
+    for _ in range(args.steps):
+        pl, _ = O.run(s, ind, scene.keyframes, k, 1, st)
+        passes += int(pl.sum())
+        k += 1
+    el = time.perf_counter() - t0
+    val = x.shape[0] * passes / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "pad4m: 4,194,304-particle press-slip-rotate sensor pad",
+                       "step": "1 IMPM substep (bounded sample of the 100-substep GPU step)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d substeps after %d warm-up substeps, FP64 oracle, serial"
+                                       % (args.steps, args.warmup)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tsim", choices=["tsim", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    from paper_2405_02914_gb300 import inputs as I
+    scene = I.scene_pad4m(seed=args.seed)
+    if args.impl == "reference":
+        return run_reference(args, scene)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2405_02914_gb300 import tsim as T
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    # inputs resident in HBM before the timed region
+    x, tag = I.gel_particles(scene.gel)
+    v, C, F = I.rest_state(x.shape[0])
+    n = x.shape[0]
+    d_in = [torch.from_numpy(a).to(dev) for a in (x, v, C, F)] + [torch.from_numpy(tag.view(np.int32)).to(dev)]
+    ctx = T.tsim_create([T.gel_desc(scene.gel)], [T.material_desc(scene.mat)], stream)
+    T.tsim_set_solver(ctx, T.solver_desc(scene.solver))
+    T.tsim_set_indenter(ctx, 0, T.indenter_desc(scene.ind))
+    T.tsim_set_trajectory(ctx, 0, scene.keyframes)
+    T.tsim_use_graph(ctx, True)
+    T.tsim_profile(ctx, True)
+    W = H = scene.readout_px
+    h_out = torch.empty((H, W), device=dev)
+    n_out = torch.empty((H, W, 3), device=dev)
+
+    def reset():
+        T.tsim_set_substep(ctx, 0)
+        T.tsim_write_particles(ctx, 0, *d_in)
+
+    def one_step():
+        T.tsim_step(ctx, SUBSTEPS_PER_STEP)
+        T.tsim_read_surface(ctx, 0, W, H, scene.readout_pitch, h_out, n_out)
+
+    reset()
+    for _ in range(args.warmup):
+        one_step()
+    reset()
+    T.tsim_kernel_time(ctx)                    # drop warm-up timings
+    s0 = T.tsim_stats(ctx)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    s1 = T.tsim_stats(ctx)
+    launches, k_ms = T.tsim_kernel_time(ctx)
+    updates = s1.particle_updates - s0.particle_updates
+    passes = s1.passes - s0.passes
+    substeps = s1.substeps - s0.substeps
+
+    # end to end through the public API with host buffers (pinned)
+    kf_host = T.keyframes(scene.keyframes)
+    h_host = torch.empty((H, W), pin_memory=True)
+    n_host = torch.empty((H, W, 3), pin_memory=True)
+    reset()
+    T.tsim_profile(ctx, False)
+    for _ in range(1):
+        T.tsim_set_trajectory(ctx, 0, kf_host)
+        T.tsim_step(ctx, SUBSTEPS_PER_STEP)
+        T.tsim_read_surface(ctx, 0, W, H, scene.readout_pitch, h_host, n_host)
+    reset()
+    s2 = T.tsim_stats(ctx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        T.tsim_set_trajectory(ctx, 0, kf_host)
+        T.tsim_step(ctx, SUBSTEPS_PER_STEP)
+        T.tsim_read_surface(ctx, 0, W, H, scene.readout_pitch, h_host, n_host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    s3 = T.tsim_stats(ctx)
+    e2e_updates = s3.particle_updates - s2.particle_updates
+    T.tsim_destroy(ctx)
+
+    # max over ranks of the time, sum of the work
+    t_max, tot_updates, e2e_max, e2e_tot = ms, updates, e2e_s, e2e_updates
+    if world > 1:
+        tt = torch.tensor([ms, e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        uu = torch.tensor([updates, e2e_updates], device=dev, dtype=torch.float64)
+        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+        t_max, e2e_max = float(tt[0]), float(tt[1])
+        tot_updates, e2e_tot = float(uu[0]), float(uu[1])
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    value = tot_updates / (t_max * 1e-3)
+    peak, peak_kind = _peaks()
+    avg_commit_ms = k_ms / max(launches, 1)
+    achieved = n * BYTES_PER_UPDATE / (avg_commit_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "pad4m: 128x128x32 cells, dx=0.3125 mm, 4,194,304 particles, "
+                               "press-slip-rotate, %d substeps + 128x128 surface readout per step"
+                               % SUBSTEPS_PER_STEP,
+                   "particles": n, "substeps_timed": int(substeps), "passes_timed": int(passes),
+                   "mean_passes_per_substep": passes / max(substeps, 1),
+                   "particle_substeps_per_s": n * substeps * world / (t_max * 1e-3),
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (particle state 436 MB per parity)",
+                   "surrogate_frames_per_s": None},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": _traffic(n),
+                     "kernel": "k_transfer<COMMIT> (fused G2P -> F,x move -> re-bin -> P2G)",
+                     "launches_timed": launches, "avg_launch_ms": avg_commit_ms,
+                     "bytes_per_launch": n * BYTES_PER_UPDATE, "peak_source": peak_kind},
+        "e2e": {"value": e2e_tot / e2e_max, "unit": UNIT, "h2d_bytes_per_step": 20 * len(kf_host),
+                "d2h_bytes_per_step": 4 * W * H * 4},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    # own kernels launched in the timed region: per substep round_begin, grid, check,
+    # commit transfer; per extra pass transfer, grid, check; per step 3 readout kernels
+    extra = passes - substeps
+    line["gpu_launches"] = int(4 * substeps + 3 * extra + 3 * args.steps) * world
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,235 @@
+/*
+ * tsim.h -- C ABI of the GB300 IMPM elastomer simulator (libtsim.so).
+ *
+ * The library advances the gel elastomer of an optical tactile sensor under
+ * a moving rigid indenter with the improved Material Point Method of
+ * "Simulation of Optical Tactile Sensors Supporting Slip and Rotation using
+ * Path Tracing and IMPM" (Sec. III-A, Eqs. 1-9, Algorithm 1).  The calls
+ * follow the paper's statement of the problem: initialise the elastomer and
+ * its material (Sec. IV-B), set the object and the pose sequence it moves
+ * along (Fig. 2 (A)-(B)), step, and read back the deformed surface that the
+ * renderer consumes (Sec. IV-B, Fig. 2 (C)).
+ *
+ * Conventions
+ *   - Every call returns an int status (TSIM_OK or a TSIM_ERR_* code) except
+ *     tsim_destroy and tsim_last_error.  On failure tsim_last_error() gives
+ *     a human-readable reason for the calling thread.
+ *   - Units are SI (metres, seconds, kilograms, pascals).  Arrays are
+ *     row-major float32 unless stated otherwise.
+ *   - A context holds n_inst independent instances (sensor pads) that
+ *     advance in lockstep.  Every instance index argument is 0..n_inst-1.
+ *   - The library owns all device state inside the opaque tsim_ctx and
+ *     allocates it in tsim_create only; no later call allocates device
+ *     memory.  The caller owns every pointer it passes.  Pointers are host
+ *     pointers when on_device == 0 and device pointers of the context's
+ *     device otherwise.
+ *   - Work is enqueued on the CUDA stream given to tsim_create (a
+ *     cudaStream_t passed as void*; NULL = legacy default stream).
+ *     tsim_step is asynchronous; device-detected errors (non-finite state,
+ *     J <= 0, a particle leaving the node box, a full cell block) are
+ *     latched per instance and returned by the next tsim_sync, tsim_stats
+ *     or tsim_read_* call, which synchronise the stream.
+ *   - Positions live in the gel frame: the block occupies
+ *     [0, cx*dx] x [0, cy*dx] x [0, cz*dx] with its base plane at z = 0.
+ *     Node (a, b, c) of the node box sits at ((a-ox)dx, (b-oy)dx, (c-oz)dx).
+ */
+#ifndef TSIM_H
+#define TSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define TSIM_OK 0
+#define TSIM_ERR_INVALID_ARG 1   /* bad argument; nothing was changed */
+#define TSIM_ERR_OOM 2           /* device allocation failed in tsim_create */
+#define TSIM_ERR_CUDA 3          /* a CUDA runtime call failed */
+#define TSIM_ERR_NUMERIC 4       /* non-finite state or J <= 0 (latched) */
+#define TSIM_ERR_DOMAIN 5        /* a particle left the node box (latched) */
+#define TSIM_ERR_CAPACITY 6      /* a cell block overflowed its slots (latched) */
+#define TSIM_ERR_STATE 7         /* calls out of order (e.g. step before particles) */
+
+/* indenter shapes (rigid analytic SDF; Sec. III-A object, Sec. IV-A indenters) */
+#define TSIM_NONE (-1)
+#define TSIM_SPHERE 0     /* p = [r] */
+#define TSIM_CYLINDER 1   /* p = [r, h, edge_round]; axis vertical, flat face down */
+#define TSIM_BOX 2        /* p = [hx, hy, hz, edge_round] (half sizes) */
+#define TSIM_PRISM 3      /* p = [side, length, edge_round]; equilateral section,
+                             apex down, extruded along the local x axis */
+#define TSIM_PERLIN 4     /* p = [hx, hy, hz, edge_round, amp, period, persistence,
+                             octaves]; rounded plate minus amp * fbm of improved
+                             noise (permutation table in perm) */
+
+/* base boundary modes */
+#define TSIM_BASE_FIXED 0 /* bottom fixed to the sensor (Sec. III-A, Algorithm 1) */
+#define TSIM_BASE_SLIP 1  /* only the normal (z) velocity is held at the base */
+#define TSIM_BASE_FREE 2  /* no base (free body; used by tests) */
+
+/* particle tag bits (low 29 bits = particle id) */
+#define TSIM_TAG_BOTTOM 0x80000000u  /* bottom cell layer: v_z = 0 after G2P */
+#define TSIM_TAG_TOP 0x40000000u     /* surface layer read by tsim_read_surface */
+#define TSIM_TAG_MARKER 0x20000000u  /* embedded marker */
+
+typedef struct tsim_ctx tsim_ctx;
+
+/* Elastomer block of cx x cy x cz cells of size dx with ppc (= 8) particles
+ * per cell, inside a node box of nx x ny x nz nodes whose node (ox, oy, oz)
+ * is the gel origin.  nx, ny, nz must be multiples of 4 (cell blocks). */
+typedef struct {
+    int cx, cy, cz;
+    int nx, ny, nz;
+    int ox, oy, oz;
+    int ppc;
+    float dx;
+} tsim_gel_desc;
+
+/* Compressible Neo-Hookean elastomer (S_p of Eq. 4): Young's modulus E,
+ * Poisson ratio nu, density rho; gravity acceleration added to the grid. */
+typedef struct {
+    float E, nu, rho;
+    float gravity[3];
+} tsim_material;
+
+/* Rigid indenter.  Its pose is given by the tip (lowest point, the
+ * calibration point x_o of Algorithm 1) and a yaw about the vertical axis
+ * through the tip; the SDF frame centre sits tip_offset above the tip.
+ * mu is the Coulomb friction coefficient of the stick/slip contact. */
+typedef struct {
+    int kind;
+    float p[8];
+    float mu;
+    float tip_offset;
+    int32_t perm[256];
+} tsim_indenter_desc;
+
+/* Pose keyframe: at substep `substep` the tip is at tip[] with yaw `yaw`
+ * (radians); poses between keyframes are linear in the substep index and
+ * held constant before the first and after the last keyframe. */
+typedef struct {
+    int32_t substep;
+    float tip[3];
+    float yaw;
+} tsim_keyframe;
+
+/* Solver: substep dt; relrest_limit = LIMIT of Algorithm 1 (1 gives plain
+ * MPM, the paper's "normal" group); relrest_threshold = its threshold;
+ * base_mode = TSIM_BASE_*; walls != 0 zeroes the velocity of the 2-node
+ * ring of the node box at +-x, +-y, +z (Sec. III-A boundary handling). */
+typedef struct {
+    float dt;
+    int relrest_limit;
+    float relrest_threshold;
+    int base_mode;
+    int walls;
+} tsim_solver_desc;
+
+typedef struct {
+    int64_t substeps;          /* substeps completed */
+    int64_t passes;            /* P2G->grid->G2P passes, summed over instances */
+    int64_t particle_updates;  /* particles x passes, summed over instances */
+    uint32_t status;           /* OR of latched device error bits of all instances */
+    int32_t n_inst;
+} tsim_stats_t;
+
+/* Create a context of n_inst instances on the current CUDA device.
+ * gels, mats: arrays of n_inst descriptors (host).  stream: cudaStream_t or
+ * NULL.  Allocates all device state: particle slots, node arrays, staging.
+ * *out is NULL on failure.  Paper: Sec. IV-B (elastomer initialisation). */
+int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_material *mats,
+                void *stream, tsim_ctx **out);
+
+/* Solver parameters shared by all instances (Algorithm 1 LIMIT/threshold,
+ * boundary handling of Sec. III-A).  Must precede tsim_write_particles. */
+int tsim_set_solver(tsim_ctx *ctx, const tsim_solver_desc *solver);
+
+/* Indenter of instance inst (host descriptor). */
+int tsim_set_indenter(tsim_ctx *ctx, int inst, const tsim_indenter_desc *ind);
+
+/* Pose keyframes of instance inst: n_kf (1..64) rows, increasing substep.
+ * Fig. 2 (B): the object moves step by step to its target pose. */
+int tsim_set_trajectory(tsim_ctx *ctx, int inst, const tsim_keyframe *kf, int n_kf,
+                        int on_device);
+
+/* Set the particle state of instance inst in particle-id order:
+ * x[n*3], v[n*3], C[n*9] (affine field, row-major), F[n*9] (deformation
+ * gradient, row-major), tag[n] (TSIM_TAG_* | id).  n must equal
+ * cx*cy*cz*ppc and ids must be 0..n-1.  Bins the particles into cell
+ * blocks and runs the particle-to-grid transfer of this state.
+ * Paper: Sec. III-A particle state (x, v, m, C, F). */
+int tsim_write_particles(tsim_ctx *ctx, int inst, const float *x, const float *v,
+                         const float *C, const float *F, const uint32_t *tag, int n,
+                         int on_device);
+
+/* Set the substep index of the next substep (the clock of the pose
+ * keyframes), for all instances.  Default 0. */
+int tsim_set_substep(tsim_ctx *ctx, int64_t k);
+
+/* Advance every instance by n_substeps IMPM time steps (Algorithm 1):
+ * passes of P2G (Eqs. 1-4), grid update with gravity, stick/slip contact,
+ * walls and fixed base (Eq. 5), G2P (Eqs. 6-7) until the relative-rest
+ * check accepts or LIMIT passes ran, then the F and x move (Eqs. 8-9).
+ * Asynchronous on the context stream. */
+int tsim_step(tsim_ctx *ctx, int n_substeps);
+
+/* Read the state of instance inst in particle-id order (any of x, v, C, F
+ * may be NULL).  v and C are those of the last completed substep.
+ * Synchronises; returns latched device errors. */
+int tsim_read_particles(tsim_ctx *ctx, int inst, float *x, float *v, float *C, float *F,
+                        int n, int on_device);
+
+/* Grid mass and momentum of instance inst after the particle-to-grid
+ * transfer of its current state (Eqs. 1-2): out[nx*ny*nz*4] holds
+ * (M_i, MG_i.x, MG_i.y, MG_i.z) per node, x fastest.  Synchronises. */
+int tsim_read_grid(tsim_ctx *ctx, int inst, float *out, int on_device);
+
+/* Surface of instance inst: height[H*W] (z of the gel surface) and unit
+ * normals normal[H*W*3] on a W x H pixel grid with pixel (u, v) centred at
+ * ((u+0.5)*pitch, (v+0.5)*pitch).  Heights are the 2-D quadratic B-spline
+ * average of the z of TSIM_TAG_TOP particles; pixels with no particle read
+ * the gel height; normals come from central differences of the height.
+ * W*H <= 1<<20.  Paper: Sec. IV-B, Fig. 2 (C) (depth map of the surface
+ * particles).  Synchronises. */
+int tsim_read_surface(tsim_ctx *ctx, int inst, float *height, float *normal, int W, int H,
+                      float pitch, int on_device);
+
+/* Positions of m particles given by id (ids[m], host) of instance inst:
+ * xyz[m*3].  Used for embedded marker tracks.  Synchronises. */
+int tsim_read_markers(tsim_ctx *ctx, int inst, const int32_t *ids, int m, float *xyz,
+                      int on_device);
+
+/* Per-substep log of instance inst for the last n substeps (n <= 4096):
+ * passes[n] taken by the relative-rest loop and calib[n] the id of the
+ * calibration particle x_e.  Either pointer may be NULL.  Synchronises. */
+int tsim_read_log(tsim_ctx *ctx, int inst, int32_t *passes, int32_t *calib, int n);
+
+/* Wait for all enqueued work; returns latched device errors. */
+int tsim_sync(tsim_ctx *ctx);
+
+/* Counters; synchronises. */
+int tsim_stats(tsim_ctx *ctx, tsim_stats_t *out);
+
+/* Capture the substep sequence in a CUDA graph with a device-driven loop
+ * over relative-rest passes (enable != 0) or launch kernels one by one. */
+int tsim_use_graph(tsim_ctx *ctx, int enable);
+
+/* Per-kernel timing with CUDA events recorded on the context stream around
+ * every launch of the fused transfer kernel (enable != 0).
+ * tsim_kernel_time returns its launches and total milliseconds since the
+ * last reset and resets the counters.  Synchronises. */
+int tsim_profile(tsim_ctx *ctx, int enable);
+int tsim_kernel_time(tsim_ctx *ctx, int64_t *launches, double *total_ms);
+
+/* Reason for the last failure on this thread (never NULL). */
+const char *tsim_last_error(void);
+
+/* Free the context and all its device memory (NULL is ignored). */
+void tsim_destroy(tsim_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSIM_H */

@@ -1,0 +1,685 @@
+// tsim_kernels.cu -- sm_103a kernels of the IMPM substep.
+//
+// One substep (Algorithm 1) for all instances in lockstep:
+//   k_round_begin     pose of substep k (and the tip at k+1), reset pass state
+//   k_grid            Eq. 5 + gravity + stick/slip SDF contact + walls + base,
+//                     one sweep over the node box; clears the P2G accumulator
+//   k_check           relative-rest check at the calibration particle x_e
+//   k_transfer<ITER>  fused G2P (Eqs. 6-7) -> P2G (Eqs. 1-4) of a repeated pass:
+//                     x and F stay, v and C go straight back to the grid
+//   k_transfer<COMMIT> fused G2P -> F, x move (Eqs. 8-9) -> re-bin into the
+//                     cell block of the new position -> P2G of the moved state
+//                     (the first pass of the next substep)
+// The velocity and affine field live on the grid between substeps; only x,
+// F and the tag persist per particle.
+#include <cuda_runtime.h>
+
+#include "tsim_device.cuh"
+#include "tsim_kernels.h"
+
+namespace tsim {
+
+__device__ __forceinline__ void atomic_or_status(InstState *S, unsigned int bits)
+{
+    atomicOr(&S->status, bits);
+}
+
+__device__ __forceinline__ long long node_of(const Inst &I, int ax, int ay, int az)
+{
+    return I.node0 + ((long long)az * I.ny + ay) * I.nx + ax;
+}
+
+// ---------------------------------------------------------------- round begin
+
+// One CTA per instance: pose of substep k (and the tip at k+1), pass state
+// reset, and x_e of Algorithm 1 -- the particle nearest to the tip x_o -- from
+// the per-block candidates written by the previous commit (or prologue).
+// Nothing in this kernel writes the global substep counters.
+__global__ void __launch_bounds__(256) k_round_begin(Dev d)
+{
+    const int inst = blockIdx.x;
+    InstState *S = d.ist + inst;
+    const Inst &I = d.inst[inst];
+    __shared__ unsigned long long s_key[8];
+    __shared__ float s_pos[8][3];
+    const long long k = d.G->k_next;
+    if (threadIdx.x == 0) {
+        Pose P;
+        pose_eval(I, d.kf + (long long)inst * MAX_KF * 5, k, P);
+        S->pose = P;
+        S->phase = 0;
+        S->pass = 0;
+    }
+    unsigned long long bk = ~0ull;
+    float bp[3] = {0.f, 0.f, 0.f};
+    for (int b = threadIdx.x; b < I.nblocks; b += blockDim.x) {
+        const Cand c = d.cand[I.block0 + b];
+        if (c.key < bk) { bk = c.key; bp[0] = c.x; bp[1] = c.y; bp[2] = c.z; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ok = __shfl_down_sync(0xffffffffu, bk, o);
+        const float o0 = __shfl_down_sync(0xffffffffu, bp[0], o);
+        const float o1 = __shfl_down_sync(0xffffffffu, bp[1], o);
+        const float o2 = __shfl_down_sync(0xffffffffu, bp[2], o);
+        if (ok < bk) { bk = ok; bp[0] = o0; bp[1] = o1; bp[2] = o2; }
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_key[w] = bk;
+        s_pos[w][0] = bp[0]; s_pos[w][1] = bp[1]; s_pos[w][2] = bp[2];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int wb = 0;
+        for (int a = 1; a < (int)(blockDim.x >> 5); ++a)
+            if (s_key[a] < s_key[wb]) wb = a;
+        S->e_id = s_key[wb] == ~0ull ? -1 : (int)(s_key[wb] & 0xffffffffull);
+        S->xe[0] = s_pos[wb][0]; S->xe[1] = s_pos[wb][1]; S->xe[2] = s_pos[wb][2];
+    }
+}
+
+__global__ void k_set_end(Dev d, long long n)
+{
+    d.G->k_end = d.G->k_next + n;
+}
+
+// ---------------------------------------------------------------- grid update
+
+__global__ void __launch_bounds__(256) k_grid(Dev d)
+{
+    const int inst = blockIdx.y;
+    InstState *S = d.ist + inst;
+    if (S->phase != 0) return;
+    const Inst &I = d.inst[inst];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // first pass of the substep: empty the destination cell-block counters
+    if (S->pass == 0 && t < I.nblocks) d.cnt[d.G->par_next ^ 1][I.block0 + t] = 0;
+    const long long nn = (long long)I.nx * I.ny * I.nz;
+    if (t >= nn) return;
+    const float4 a = d.acc[I.node0 + t];
+    if (!(a.x > 0.f)) return;
+    const int ax = (int)(t % I.nx), ay = (int)((t / I.nx) % I.ny), az = (int)(t / ((long long)I.nx * I.ny));
+    float V[3] = {a.y / a.x + I.dt * I.g[0], a.z / a.x + I.dt * I.g[1], a.w / a.x + I.dt * I.g[2]};
+    if (I.ind_kind != K_NONE) {
+        const Pose &P = S->pose;
+        float xw[3] = {(ax - I.ox) * I.dx, (ay - I.oy) * I.dx, (az - I.oz) * I.dx};
+        float n[3];
+        float phi = sdf_world(I, d.perm + inst * 256, P, xw, n);
+        if (phi <= 0.f) {
+            float vo[3];
+            object_velocity(P, xw, vo);
+            float vr[3] = {V[0] - vo[0], V[1] - vo[1], V[2] - vo[2]};
+            float vn = vr[0] * n[0] + vr[1] * n[1] + vr[2] * n[2];
+            if (vn < 0.f) {
+                float vt[3] = {vr[0] - vn * n[0], vr[1] - vn * n[1], vr[2] - vn * n[2]};
+                float vtl = sqrtf(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+                float lim = I.fric * (-vn);
+                float sc = vtl <= lim ? 0.f : 1.f - lim / vtl;   // rest or Coulomb slip
+#pragma unroll
+                for (int r = 0; r < 3; ++r) V[r] = vt[r] * sc + vo[r];
+            }
+        }
+    }
+    if (I.walls && (ax < 2 || ay < 2 || ax >= I.nx - 2 || ay >= I.ny - 2 || az >= I.nz - 2))
+        V[0] = V[1] = V[2] = 0.f;
+    if (az - I.oz <= 0) {
+        if (I.base_mode == BASE_FIXED) V[0] = V[1] = V[2] = 0.f;
+        else if (I.base_mode == BASE_SLIP) V[2] = 0.f;
+    }
+    d.vel[I.node0 + t] = make_float4(V[0], V[1], V[2], 0.f);
+    d.acc[I.node0 + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// ---------------------------------------------------------------- relative-rest check
+
+// Single CTA.  On the first pass of a substep it also advances the global
+// substep counters.  Each instance still iterating compares the tangential
+// velocity at x_e with the object's (Algorithm 1) and either commits or asks
+// for another pass; a pass count >= LIMIT always commits, so the device-driven
+// loop of the graph ends after at most LIMIT passes.  Thread 0 alone sets the
+// loop condition, once per launch.
+__global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle h, int use_cond)
+{
+    __shared__ int s_any;
+    __shared__ int s_first;
+    if (threadIdx.x == 0) {
+        s_any = 0;
+        s_first = d.ist[0].pass == 0 && d.ist[0].phase == 0;
+    }
+    __syncthreads();
+    for (int inst = threadIdx.x; inst < d.n_inst; inst += blockDim.x) {
+        InstState *S = d.ist + inst;
+        const Inst &I = d.inst[inst];
+        const int ph = S->phase;
+        if (ph == 1) { S->phase = 2; continue; }
+        if (ph != 0) continue;
+        bool accept = true;
+        const Pose &P = S->pose;
+        if (I.ind_kind != K_NONE && S->e_id >= 0) {
+            const float xe[3] = {S->xe[0], S->xe[1], S->xe[2]};
+            float n[3];
+            const float phi = sdf_world(I, d.perm + inst * 256, P, xe, n);
+            if (phi <= I.dx) {
+                float vo[3];
+                object_velocity(P, xe, vo);
+                const float vot = sqrtf(vo[0] * vo[0] + vo[1] * vo[1]);
+                if (vot >= 1e-6f) {
+                    // G2P (Eq. 6) of the tangential velocity at x_e
+                    int base[3];
+                    float f[3], w[3][3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) bspline(xe[a], I.inv_dx, base[a], f[a], w[a]);
+                    float ve0 = 0.f, ve1 = 0.f;
+                    const int ax0 = base[0] + I.ox, ay0 = base[1] + I.oy, az0 = base[2] + I.oz;
+                    if (ax0 >= 0 && ay0 >= 0 && az0 >= 0 && ax0 + 2 < I.nx && ay0 + 2 < I.ny && az0 + 2 < I.nz) {
+                        for (int i = 0; i < 3; ++i)
+                            for (int j = 0; j < 3; ++j)
+                                for (int k = 0; k < 3; ++k) {
+                                    const float4 V = d.vel[node_of(I, ax0 + i, ay0 + j, az0 + k)];
+                                    const float wt = w[0][i] * w[1][j] * w[2][k];
+                                    ve0 += wt * V.x;
+                                    ve1 += wt * V.y;
+                                }
+                    }
+                    const float a = ve0 - vo[0], b = ve1 - vo[1];
+                    accept = sqrtf(a * a + b * b) <= I.threshold * vot;
+                }
+            }
+        }
+        const int pass = S->pass + 1;
+        S->pass = pass;
+        S->passes_total += 1;
+        if (accept || pass >= I.limit) {
+            S->phase = 1;
+            const long long s = S->substeps;
+            d.log[(long long)inst * LOGN + (s % LOGN)] = make_int2(pass, S->e_id);
+            S->substeps = s + 1;
+        } else {
+            atomicOr(&s_any, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_first) {
+            const long long k = d.G->k_next;
+            const int par = d.G->par_next;
+            d.G->k_cur = k;
+            d.G->par_cur = par;
+            d.G->k_next = k + 1;
+            d.G->par_next = par ^ 1;
+        }
+        if (use_cond) cudaGraphSetConditional(h, s_any ? 1u : 0u);
+    }
+}
+
+// ---------------------------------------------------------------- fused transfer
+
+enum { MODE_PROLOGUE = 0, MODE_ITER = 1, MODE_COMMIT = 2 };
+
+template <int MODE>
+__global__ void __launch_bounds__(NT) k_transfer(Dev d, int block_offset)
+{
+    __shared__ float4 sV[GV * GV * GV];
+    __shared__ float sA[4][GA * GA * GA];
+    __shared__ unsigned long long s_key[NT / 32];
+    __shared__ float s_pos[NT / 32][3];
+    __shared__ float s_tip[3];
+
+    const int b = block_offset + blockIdx.x;
+    const int inst = d.blk_inst[b];
+    InstState *S = d.ist + inst;
+    int par;
+    if (MODE == MODE_PROLOGUE) {
+        if (!S->dirty) return;
+        par = d.G->par_next;
+    } else {
+        const int ph = S->phase;
+        if (MODE == MODE_ITER && ph != 0) return;
+        if (MODE == MODE_COMMIT && ph != 1) return;
+        par = d.G->par_cur;
+    }
+    const bool moves = MODE == MODE_COMMIT;
+    const bool cands = MODE != MODE_ITER;
+    const Inst &I = d.inst[inst];
+    const int count = min(d.cnt[par][b], CAP);          // an overflowed block was latched as an error
+    if (count == 0 && !cands) return;
+
+    const int lb = b - I.block0;
+    const int gx0 = (lb % I.nbx) * BLK, gy0 = ((lb / I.nbx) % I.nby) * BLK, gz0 = (lb / (I.nbx * I.nby)) * BLK;
+    const float dx = I.dx, inv_dx = I.inv_dx, dt = I.dt;
+
+    if (MODE != MODE_PROLOGUE) {
+        for (int t = threadIdx.x; t < GV * GV * GV; t += NT) {
+            const int lx = t % GV, ly = (t / GV) % GV, lz = t / (GV * GV);
+            const int ax = gx0 + lx, ay = gy0 + ly, az = gz0 + lz;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ax < I.nx && ay < I.ny && az < I.nz) v = d.vel[node_of(I, ax, ay, az)];
+            sV[t] = v;
+        }
+    }
+    for (int t = threadIdx.x; t < GA * GA * GA; t += NT) {
+        sA[0][t] = 0.f; sA[1][t] = 0.f; sA[2][t] = 0.f; sA[3][t] = 0.f;
+    }
+    if (threadIdx.x == 0) {
+        if (MODE == MODE_PROLOGUE) {
+            double t4[4], v4[4];
+            pose_tip(d.kf + (long long)inst * MAX_KF * 5, I.nkf, d.G->k_next, t4, v4, (double)dt);
+            s_tip[0] = (float)t4[0]; s_tip[1] = (float)t4[1]; s_tip[2] = (float)t4[2];
+        } else {
+            s_tip[0] = S->pose.tip_next[0]; s_tip[1] = S->pose.tip_next[1]; s_tip[2] = S->pose.tip_next[2];
+        }
+    }
+    __syncthreads();
+
+    const long long SS = d.S;
+    const float *src = d.P[par];
+    const uint32_t *srcT = d.T[par];
+    float *dst = d.P[par ^ 1];
+    uint32_t *dstT = d.T[par ^ 1];
+    int *cntDst = d.cnt[par ^ 1];
+    const bool store_vc = moves && (d.G->k_cur + 1 == d.G->k_end);
+    const float tip0 = s_tip[0], tip1 = s_tip[1], tip2 = s_tip[2];
+    const int lane = threadIdx.x & 31;
+    unsigned long long best = ~0ull;
+    float bpos[3] = {0.f, 0.f, 0.f};
+    unsigned int err = 0;
+
+    for (int r0 = 0; r0 < count; r0 += NT) {
+        const int r = r0 + threadIdx.x;
+        bool valid = r < count;
+        const long long slot = (long long)b * CAP + r;
+        float x[3], F[9], v[3] = {0.f, 0.f, 0.f}, C[9];
+        uint32_t tag = 0;
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x[c] = src[c * SS + slot];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) F[c] = src[(3 + c) * SS + slot];
+            tag = srcT[slot];
+            if (MODE == MODE_PROLOGUE) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] = d.VC[c * SS + slot];
+#pragma unroll
+                for (int c = 0; c < 9; ++c) C[c] = d.VC[(3 + c) * SS + slot];
+            } else {
+                // G2P: v = sum w V (Eq. 6), C = 4/dx^2 sum w V (x_i - x_p)^T (Eq. 7)
+                int base[3];
+                float f[3], w[3][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) bspline(x[a], inv_dx, base[a], f[a], w[a]);
+                const int lx = base[0] + I.ox - gx0, ly = base[1] + I.oy - gy0, lz = base[2] + I.oz - gz0;
+                if (lx < 0 || ly < 0 || lz < 0 || lx >= BLK || ly >= BLK || lz >= BLK) {
+                    err |= ST_DOMAIN;
+                    valid = false;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) C[c] = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                const float4 Vn = sV[((lz + k) * GV + (ly + j)) * GV + (lx + i)];
+                                const float wt = w[0][i] * w[1][j] * w[2][k];
+                                const float d0 = ((float)i - f[0]), d1 = ((float)j - f[1]), d2 = ((float)k - f[2]);
+                                const float wv0 = wt * Vn.x, wv1 = wt * Vn.y, wv2 = wt * Vn.z;
+                                v[0] += wv0; v[1] += wv1; v[2] += wv2;
+                                C[0] += wv0 * d0; C[1] += wv0 * d1; C[2] += wv0 * d2;
+                                C[3] += wv1 * d0; C[4] += wv1 * d1; C[5] += wv1 * d2;
+                                C[6] += wv2 * d0; C[7] += wv2 * d1; C[8] += wv2 * d2;
+                            }
+                    const float s4 = 4.f * inv_dx;   // (4/dx^2) * dx: d above is in cells
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) C[c] *= s4;
+                    if ((tag & TAG_BOTTOM) && I.base_mode != BASE_FREE) v[2] = 0.f;   // Algorithm 1
+                }
+            }
+        }
+        if (valid && moves) {
+            // F <- (I + dt C) F (Eq. 8); x <- x + dt v (Eq. 9)
+            float Fn[9];
+#pragma unroll
+            for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc)
+                    Fn[rr * 3 + cc] = F[rr * 3 + cc] + dt * (C[rr * 3] * F[cc] + C[rr * 3 + 1] * F[3 + cc] +
+                                                             C[rr * 3 + 2] * F[6 + cc]);
+#pragma unroll
+            for (int c = 0; c < 9; ++c) F[c] = Fn[c];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x[c] += dt * v[c];
+        }
+        // stress (S_p of Eq. 4) of the state that enters P2G
+        float tau[9];
+        int nbase[3] = {0, 0, 0};
+        float nf[3] = {0.f, 0.f, 0.f}, nw[3][3];
+        if (valid) {
+            const float J = kirchhoff(F, I.mu, I.lam, tau);
+            if (!(J > 0.f) || !isfinite(J) || !isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2])) {
+                err |= ST_NUMERIC;
+                valid = false;
+            }
+        }
+        if (valid) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) bspline(x[a], inv_dx, nbase[a], nf[a], nw[a]);
+            const int ax = nbase[0] + I.ox, ay = nbase[1] + I.oy, az = nbase[2] + I.oz;
+            const int wx = ax - (gx0 - 1), wy = ay - (gy0 - 1), wz = az - (gz0 - 1);
+            if (ax < 0 || ay < 0 || az < 0 || ax + 2 >= I.nx || ay + 2 >= I.ny || az + 2 >= I.nz ||
+                wx < 0 || wy < 0 || wz < 0 || wx + 2 >= GA || wy + 2 >= GA || wz + 2 >= GA) {
+                err |= ST_DOMAIN;
+                valid = false;
+            } else {
+                // P2G: M += w m (Eq. 1); MG += w (m v + m C d) - 4 dt/dx^2 V0 w tau d (Eqs. 2-4)
+                float Q[9];
+#pragma unroll
+                for (int c = 0; c < 9; ++c) Q[c] = (I.mp * C[c] + I.kME * tau[c]) * dx;   // d below in cells
+                const float mv0 = I.mp * v[0], mv1 = I.mp * v[1], mv2 = I.mp * v[2];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const float wt = nw[0][i] * nw[1][j] * nw[2][k];
+                            const float d0 = (float)i - nf[0], d1 = (float)j - nf[1], d2 = (float)k - nf[2];
+                            const int n = ((wz + k) * GA + (wy + j)) * GA + (wx + i);
+                            atomicAdd(&sA[0][n], wt * I.mp);
+                            atomicAdd(&sA[1][n], wt * (mv0 + Q[0] * d0 + Q[1] * d1 + Q[2] * d2));
+                            atomicAdd(&sA[2][n], wt * (mv1 + Q[3] * d0 + Q[4] * d1 + Q[5] * d2));
+                            atomicAdd(&sA[3][n], wt * (mv2 + Q[6] * d0 + Q[7] * d1 + Q[8] * d2));
+                        }
+            }
+        }
+        if (moves) {
+            // re-bin into the cell block of the new position: warp-aggregated slot claims
+            unsigned int key = 0xffffffffu;
+            if (valid) {
+                const int ax = nbase[0] + I.ox, ay = nbase[1] + I.oy, az = nbase[2] + I.oz;
+                key = (unsigned int)(I.block0 + ((az / BLK) * I.nby + (ay / BLK)) * I.nbx + (ax / BLK));
+            }
+            const unsigned int peers = __match_any_sync(0xffffffffu, key);
+            const int leader = __ffs(peers) - 1;
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            int basepos = 0;
+            if (lane == leader && key != 0xffffffffu) basepos = atomicAdd(&cntDst[key], __popc(peers));
+            basepos = __shfl_sync(0xffffffffu, basepos, leader);
+            if (valid) {
+                const int rr = basepos + rank;
+                if (rr >= CAP) {
+                    err |= ST_CAPACITY;
+                } else {
+                    const long long ds = (long long)key * CAP + rr;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) dst[c * SS + ds] = x[c];
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) dst[(3 + c) * SS + ds] = F[c];
+                    dstT[ds] = tag;
+                    if (store_vc) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) d.VC[c * SS + ds] = v[c];
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) d.VC[(3 + c) * SS + ds] = C[c];
+                    }
+                }
+            }
+        }
+        if (cands && valid) {
+            const float e0 = x[0] - tip0, e1 = x[1] - tip1, e2 = x[2] - tip2;
+            const float dd = e0 * e0 + e1 * e1 + e2 * e2;
+            const unsigned long long kk = ((unsigned long long)__float_as_uint(dd) << 32) | (tag & ID_MASK);
+            if (kk < best) { best = kk; bpos[0] = x[0]; bpos[1] = x[1]; bpos[2] = x[2]; }
+        }
+    }
+    if (err) atomic_or_status(S, err);
+    __syncthreads();
+    // flush the block-local grid window: one vector atomic per touched node
+    for (int t = threadIdx.x; t < GA * GA * GA; t += NT) {
+        const float m = sA[0][t];
+        if (m != 0.f) {
+            const int ax = gx0 - 1 + t % GA, ay = gy0 - 1 + (t / GA) % GA, az = gz0 - 1 + t / (GA * GA);
+            if (ax >= 0 && ay >= 0 && az >= 0 && ax < I.nx && ay < I.ny && az < I.nz)
+                atomicAdd(&d.acc[node_of(I, ax, ay, az)], make_float4(m, sA[1][t], sA[2][t], sA[3][t]));
+        }
+    }
+    if (cands) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ok = __shfl_down_sync(0xffffffffu, best, o);
+            const float o0 = __shfl_down_sync(0xffffffffu, bpos[0], o);
+            const float o1 = __shfl_down_sync(0xffffffffu, bpos[1], o);
+            const float o2 = __shfl_down_sync(0xffffffffu, bpos[2], o);
+            if (ok < best) { best = ok; bpos[0] = o0; bpos[1] = o1; bpos[2] = o2; }
+        }
+        if (lane == 0) {
+            s_key[threadIdx.x >> 5] = best;
+            s_pos[threadIdx.x >> 5][0] = bpos[0];
+            s_pos[threadIdx.x >> 5][1] = bpos[1];
+            s_pos[threadIdx.x >> 5][2] = bpos[2];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int wbest = 0;
+            for (int a = 1; a < NT / 32; ++a)
+                if (s_key[a] < s_key[wbest]) wbest = a;
+            Cand c;
+            c.key = s_key[wbest];
+            c.x = s_pos[wbest][0]; c.y = s_pos[wbest][1]; c.z = s_pos[wbest][2]; c.pad = 0.f;
+            d.cand[b] = c;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- staging <-> slots
+
+__global__ void k_bin_staged(Dev d, int inst, int par)
+{
+    const Inst &I = d.inst[inst];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= I.n_particles) return;
+    const long long sid = I.id0 + t;
+    float x[3] = {d.sx[sid * 3], d.sx[sid * 3 + 1], d.sx[sid * 3 + 2]};
+    int ab[3];
+    const int nn[3] = {I.nx, I.ny, I.nz}, oo[3] = {I.ox, I.oy, I.oz};
+    bool ok = isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int base;
+        float f, w[3];
+        bspline(x[a], I.inv_dx, base, f, w);
+        ab[a] = base + oo[a];
+        if (ab[a] < 0 || ab[a] + 2 >= nn[a]) ok = false;
+    }
+    const uint32_t tag = d.stag[sid];
+    if ((tag & ID_MASK) >= (uint32_t)I.n_particles) ok = false;
+    if (!ok) {
+        atomic_or_status(d.ist + inst, ST_DOMAIN);
+        return;
+    }
+    const int blk = I.block0 + ((ab[2] / BLK) * I.nby + ab[1] / BLK) * I.nbx + ab[0] / BLK;
+    const int r = atomicAdd(&d.cnt[par][blk], 1);
+    if (r >= CAP) {
+        atomic_or_status(d.ist + inst, ST_CAPACITY);
+        return;
+    }
+    const long long SS = d.S, slot = (long long)blk * CAP + r;
+    float *P = d.P[par];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) P[c * SS + slot] = x[c];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) P[(3 + c) * SS + slot] = d.sF[sid * 9 + c];
+    d.T[par][slot] = tag;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d.VC[c * SS + slot] = d.sv[sid * 3 + c];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) d.VC[(3 + c) * SS + slot] = d.sC[sid * 9 + c];
+}
+
+__global__ void k_gather(Dev d, int inst, int par)
+{
+    const Inst &I = d.inst[inst];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)I.nblocks * CAP) return;
+    const int b = I.block0 + (int)(t / CAP), r = (int)(t % CAP);
+    if (r >= d.cnt[par][b]) return;
+    const long long SS = d.S, slot = (long long)b * CAP + r;
+    const uint32_t tag = d.T[par][slot];
+    const uint32_t id = tag & ID_MASK;
+    if (id >= (uint32_t)I.n_particles) {
+        atomic_or_status(d.ist + inst, ST_DOMAIN);
+        return;
+    }
+    const long long sid = I.id0 + id;
+    const float *P = d.P[par];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d.sx[sid * 3 + c] = P[c * SS + slot];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) d.sF[sid * 9 + c] = P[(3 + c) * SS + slot];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d.sv[sid * 3 + c] = d.VC[c * SS + slot];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) d.sC[sid * 9 + c] = d.VC[(3 + c) * SS + slot];
+    d.stag[sid] = tag;
+}
+
+__global__ void k_pick(Dev d, int inst, const int *ids, int m, float *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    const Inst &I = d.inst[inst];
+    const int id = ids[t];
+    if (id < 0 || id >= I.n_particles) {
+        out[t * 3] = out[t * 3 + 1] = out[t * 3 + 2] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const long long sid = I.id0 + id;
+    out[t * 3] = d.sx[sid * 3];
+    out[t * 3 + 1] = d.sx[sid * 3 + 1];
+    out[t * 3 + 2] = d.sx[sid * 3 + 2];
+}
+
+// ---------------------------------------------------------------- surface readout
+
+__device__ __forceinline__ float bspline_kernel(float t)
+{
+    t = fabsf(t);
+    if (t < 0.5f) return 0.75f - t * t;
+    if (t < 1.5f) { const float a = 1.5f - t; return 0.5f * a * a; }
+    return 0.f;
+}
+
+__global__ void k_surface_splat(Dev d, int inst, int par, float *num, float *den, int W, int H,
+                                float inv_pitch)
+{
+    const Inst &I = d.inst[inst];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)I.nblocks * CAP) return;
+    const int b = I.block0 + (int)(t / CAP), r = (int)(t % CAP);
+    if (r >= d.cnt[par][b]) return;
+    const long long SS = d.S, slot = (long long)b * CAP + r;
+    if (!(d.T[par][slot] & TAG_TOP)) return;
+    const float *P = d.P[par];
+    const float x = P[slot], y = P[SS + slot], z = P[2 * SS + slot];
+    const float px = x * inv_pitch - 0.5f, py = y * inv_pitch - 0.5f;
+    const int u0 = (int)floorf(px) - 1, v0 = (int)floorf(py) - 1;
+    for (int bb = v0; bb <= v0 + 3; ++bb) {
+        if (bb < 0 || bb >= H) continue;
+        const float wy = bspline_kernel(py - (float)bb);
+        if (wy == 0.f) continue;
+        for (int a = u0; a <= u0 + 3; ++a) {
+            if (a < 0 || a >= W) continue;
+            const float w = bspline_kernel(px - (float)a) * wy;
+            if (w == 0.f) continue;
+            atomicAdd(num + (long long)bb * W + a, w * z);
+            atomicAdd(den + (long long)bb * W + a, w);
+        }
+    }
+}
+
+__global__ void k_surface_height(const float *num, const float *den, float *h, int WH, float h_empty)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < WH) h[t] = den[t] > 0.f ? num[t] / den[t] : h_empty;
+}
+
+__global__ void k_surface_normal(const float *h, float *nrm, int W, int H, float pitch)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= W * H) return;
+    const int a = t % W, b = t / W;
+    const int al = a > 0 ? a - 1 : a, ar = a < W - 1 ? a + 1 : a;
+    const int bl = b > 0 ? b - 1 : b, br = b < H - 1 ? b + 1 : b;
+    const float hx = (h[b * W + ar] - h[b * W + al]) / ((float)(ar - al) * pitch);
+    const float hy = (h[br * W + a] - h[bl * W + a]) / ((float)(br - bl) * pitch);
+    const float L = rsqrtf(hx * hx + hy * hy + 1.f);
+    nrm[t * 3] = -hx * L;
+    nrm[t * 3 + 1] = -hy * L;
+    nrm[t * 3 + 2] = L;
+}
+
+// ---------------------------------------------------------------- launchers
+
+static inline unsigned int cdiv(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
+
+void launch_round_begin(const Dev &d, cudaStream_t s) { k_round_begin<<<d.n_inst, 256, 0, s>>>(d); }
+void launch_set_end(const Dev &d, long long n, cudaStream_t s) { k_set_end<<<1, 1, 0, s>>>(d, n); }
+
+void launch_grid(const Dev &d, long long max_nodes, cudaStream_t s)
+{
+    dim3 g(cdiv(max_nodes, 256), d.n_inst);
+    k_grid<<<g, 256, 0, s>>>(d);
+}
+
+void launch_check(const Dev &d, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s)
+{
+    k_check<<<1, 256, 0, s>>>(d, h, use_cond);
+}
+
+void launch_transfer(const Dev &d, int mode, int block_offset, int nblocks, cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+    if (mode == MODE_PROLOGUE) k_transfer<MODE_PROLOGUE><<<nblocks, NT, 0, s>>>(d, block_offset);
+    else if (mode == MODE_ITER) k_transfer<MODE_ITER><<<nblocks, NT, 0, s>>>(d, block_offset);
+    else k_transfer<MODE_COMMIT><<<nblocks, NT, 0, s>>>(d, block_offset);
+}
+
+void launch_bin_staged(const Dev &d, int inst, int n, int par, cudaStream_t s)
+{
+    k_bin_staged<<<cdiv(n, 256), 256, 0, s>>>(d, inst, par);
+}
+
+void launch_gather(const Dev &d, int inst, int nblocks, int par, cudaStream_t s)
+{
+    k_gather<<<cdiv((long long)nblocks * CAP, 256), 256, 0, s>>>(d, inst, par);
+}
+
+void launch_pick(const Dev &d, int inst, const int *ids, int m, float *out, cudaStream_t s)
+{
+    k_pick<<<cdiv(m, 128), 128, 0, s>>>(d, inst, ids, m, out);
+}
+
+void launch_surface(const Dev &d, int inst, int nblocks, int par, float *num, float *den, float *h,
+                    float *nrm, int W, int H, float pitch, float h_empty, cudaStream_t s)
+{
+    cudaMemsetAsync(num, 0, sizeof(float) * (size_t)W * H, s);
+    cudaMemsetAsync(den, 0, sizeof(float) * (size_t)W * H, s);
+    k_surface_splat<<<cdiv((long long)nblocks * CAP, 256), 256, 0, s>>>(d, inst, par, num, den, W, H,
+                                                                          1.f / pitch);
+    k_surface_height<<<cdiv((long long)W * H, 256), 256, 0, s>>>(num, den, h, W * H, h_empty);
+    k_surface_normal<<<cdiv((long long)W * H, 256), 256, 0, s>>>(h, nrm, W, H, pitch);
+}
+
+// kernel handles for graph construction
+void *fn_round_begin() { return (void *)k_round_begin; }
+void *fn_grid() { return (void *)k_grid; }
+void *fn_check() { return (void *)k_check; }
+void *fn_transfer(int mode)
+{
+    if (mode == MODE_PROLOGUE) return (void *)k_transfer<MODE_PROLOGUE>;
+    if (mode == MODE_ITER) return (void *)k_transfer<MODE_ITER>;
+    return (void *)k_transfer<MODE_COMMIT>;
+}
+
+}  // namespace tsim

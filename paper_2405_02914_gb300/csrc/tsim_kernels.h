@@ -1,0 +1,27 @@
+// tsim_kernels.h -- host-side launchers of the sm_103a kernels (tsim_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "tsim_device.cuh"
+
+namespace tsim {
+
+enum { MODE_PROLOGUE_ = 0, MODE_ITER_ = 1, MODE_COMMIT_ = 2 };
+
+void launch_round_begin(const Dev &d, cudaStream_t s);
+void launch_set_end(const Dev &d, long long n, cudaStream_t s);
+void launch_grid(const Dev &d, long long max_nodes, cudaStream_t s);
+void launch_check(const Dev &d, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
+void launch_transfer(const Dev &d, int mode, int block_offset, int nblocks, cudaStream_t s);
+void launch_bin_staged(const Dev &d, int inst, int n, int par, cudaStream_t s);
+void launch_gather(const Dev &d, int inst, int nblocks, int par, cudaStream_t s);
+void launch_pick(const Dev &d, int inst, const int *ids, int m, float *out, cudaStream_t s);
+void launch_surface(const Dev &d, int inst, int nblocks, int par, float *num, float *den, float *h,
+                    float *nrm, int W, int H, float pitch, float h_empty, cudaStream_t s);
+
+void *fn_round_begin();
+void *fn_grid();
+void *fn_check();
+void *fn_transfer(int mode);
+
+}  // namespace tsim

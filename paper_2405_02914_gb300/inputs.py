@@ -65,8 +65,8 @@ class Gel:
 
     @property
     def nodes(self):
-        """Node box dims (nx, ny, nz); multiples of 4 when cx, cy are."""
-        return (self.cx + 2 * NODE_PAD, self.cy + 2 * NODE_PAD,
+        """Node box dims (nx, ny, nz), rounded up to whole 4-node blocks."""
+        return (_round_up(self.cx + 2 * NODE_PAD, 4), _round_up(self.cy + 2 * NODE_PAD, 4),
                 _round_up(self.cz + NODE_PAD + TOP_HEADROOM, 4))
 
     @property

@@ -1,0 +1,88 @@
+"""The C-ABI library builds, loads and exports every call of include/tsim.h.
+
+CPU only: nothing here launches a kernel.  Struct layouts of the ctypes
+binding are checked against the C header compiled with gcc.
+"""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2405_02914_gb300 import tsim
+from paper_2405_02914_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tsim.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tsim_[a-z_]+)\s*\(", src)))
+
+
+def test_library_builds_and_loads():
+    path = B.build()
+    assert os.path.exists(path)
+    tsim.load()
+
+
+def test_exports_every_declared_symbol():
+    names = _declared()
+    assert len(names) >= 19
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (tsim_[a-z_]+)$", out, flags=re.M))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    assert set(names) == set(tsim.EXPORTS)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "tsim.h"\n'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(tsim_gel_desc),'
+                    'sizeof(tsim_material), sizeof(tsim_indenter_desc), sizeof(tsim_keyframe),'
+                    'sizeof(tsim_solver_desc), sizeof(tsim_stats_t), offsetof(tsim_indenter_desc, perm));'
+                    'return 0;}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
+    got = [int(a) for a in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [C.sizeof(tsim.GelDesc), C.sizeof(tsim.MaterialDesc), C.sizeof(tsim.IndenterDesc),
+            C.sizeof(tsim.Keyframe), C.sizeof(tsim.SolverDesc), C.sizeof(tsim.Stats),
+            tsim.IndenterDesc.perm.offset]
+    assert got == want
+
+
+def test_invalid_arguments_rejected_without_gpu():
+    L = tsim.load()
+    out = C.c_void_p()
+    g = tsim.GelDesc()
+    m = tsim.MaterialDesc()
+    assert L.tsim_create(0, C.byref(g), C.byref(m), None, C.byref(out)) == 1
+    assert out.value is None
+    assert "instances" in L.tsim_last_error().decode()
+    assert L.tsim_step(None, 1) == 1
+    assert L.tsim_sync(None) == 1
+    assert L.tsim_read_log(None, 0, None, None, 1) == 1
+    # a node box that is not a multiple of 4 is rejected before any allocation
+    g.cx, g.cy, g.cz, g.nx, g.ny, g.nz, g.ox, g.oy, g.oz, g.ppc, g.dx = 4, 4, 4, 13, 12, 16, 4, 4, 4, 8, 1e-3
+    m.E, m.nu, m.rho = 1e5, 0.4, 1000.0
+    assert L.tsim_create(1, C.byref(g), C.byref(m), None, C.byref(out)) == 1
+    L.tsim_destroy(None)
+
+
+def test_descriptors_from_inputs():
+    from paper_2405_02914_gb300 import inputs as I
+    sc = I.scene_pad4m(seed=1)
+    g = tsim.gel_desc(sc.gel)
+    assert (g.nx, g.ny, g.nz) == (136, 136, 44) and g.cx == 128
+    ind = tsim.indenter_desc(sc.ind)
+    assert ind.kind == I.CYLINDER and abs(ind.tip_offset - 5e-3) < 1e-9
+    kf = tsim.keyframes(sc.keyframes)
+    assert len(kf) == 4 and kf[3].substep == 20000
+    for cx in (5, 13, 31):
+        nx, ny, nz = I.Gel(cx, cx + 2, 3, 1e-3).nodes
+        assert nx % 4 == 0 and ny % 4 == 0 and nz % 4 == 0 and nx >= cx + 8
