@@ -175,6 +175,8 @@ def main():
     ap.add_argument("--impl", default="tsim", choices=["tsim", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch kernels one by one (profilers cannot see inside graphs with loops)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -206,7 +208,7 @@ def main():
     T.tsim_set_solver(ctx, T.solver_desc(scene.solver))
     T.tsim_set_indenter(ctx, 0, T.indenter_desc(scene.ind))
     T.tsim_set_trajectory(ctx, 0, scene.keyframes)
-    T.tsim_use_graph(ctx, True)
+    T.tsim_use_graph(ctx, not args.no_graph)
     T.tsim_profile(ctx, True)
     W = H = scene.readout_px
     h_out = torch.empty((H, W), device=dev)

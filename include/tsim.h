@@ -26,7 +26,8 @@
  *   - Work is enqueued on the CUDA stream given to tsim_create (a
  *     cudaStream_t passed as void*; NULL = legacy default stream).
  *     tsim_step is asynchronous; device-detected errors (non-finite state,
- *     J <= 0, a particle leaving the node box, a full cell block) are
+ *     J <= 0, a particle leaving the node box, a full cell block, a device
+ *     wait that gave up) are
  *     latched per instance and returned by the next tsim_sync, tsim_stats
  *     or tsim_read_* call, which synchronise the stream.
  *   - Positions live in the gel frame: the block occupies
@@ -51,6 +52,7 @@ extern "C" {
 #define TSIM_ERR_DOMAIN 5        /* a particle left the node box (latched) */
 #define TSIM_ERR_CAPACITY 6      /* a cell block overflowed its slots (latched) */
 #define TSIM_ERR_STATE 7         /* calls out of order (e.g. step before particles) */
+#define TSIM_ERR_TIMEOUT 8       /* a bounded device wait gave up (latched) */
 
 /* indenter shapes (rigid analytic SDF; Sec. III-A object, Sec. IV-A indenters) */
 #define TSIM_NONE (-1)

@@ -176,6 +176,13 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
         delete c;
         return fail(TSIM_ERR_INVALID_ARG, "problem too large");
     }
+    {
+        cudaError_t e = setup_kernels();
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(TSIM_ERR_CUDA, std::string("kernel setup: ") + cudaGetErrorString(e));
+        }
+    }
     c->total_blocks = blocks;
     c->total_nodes = nodes;
     c->total_particles = parts;
@@ -459,13 +466,13 @@ static int launch_substeps_stream(tsim_ctx *c, int n)
 }
 
 static int add_kernel(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_t *deps, int ndeps, void *fn,
-                      dim3 grid, dim3 block, void **args)
+                      dim3 grid, dim3 block, void **args, size_t shmem = 0)
 {
     cudaKernelNodeParams p{};
     p.func = fn;
     p.gridDim = grid;
     p.blockDim = block;
-    p.sharedMemBytes = 0;
+    p.sharedMemBytes = (unsigned int)shmem;
     p.kernelParams = args;
     p.extra = nullptr;
     CU(cudaGraphAddKernelNode(node, g, deps, ndeps, &p));
@@ -512,7 +519,7 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
         CU(cudaGraphAddNode(&n_while, g, &n_chk, nullptr, 1, &wp));
         cudaGraph_t body = wp.conditional.phGraph_out[0];
         cudaGraphNode_t b_tr, b_grid, b_chk;
-        rc = add_kernel(body, &b_tr, nullptr, 0, fn_transfer(MODE_ITER_), tr_grid, tr_blk, a_tr);
+        rc = add_kernel(body, &b_tr, nullptr, 0, fn_transfer(MODE_ITER_), tr_grid, tr_blk, a_tr, transfer_smem_bytes());
         if (rc) break;
         rc = add_kernel(body, &b_grid, &b_tr, 1, fn_grid(), grid_grid, grid_blk, a_grid);
         if (rc) break;
@@ -528,7 +535,8 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
             CU(cudaGraphAddEventRecordNode(&n_ev0, g, &last, 1, e0));
             last = n_ev0;
         }
-        rc = add_kernel(g, &n_commit, &last, 1, fn_transfer(MODE_COMMIT_), tr_grid, tr_blk, a_tr);
+        rc = add_kernel(g, &n_commit, &last, 1, fn_transfer(MODE_COMMIT_), tr_grid, tr_blk, a_tr,
+                        transfer_smem_bytes());
         if (rc) break;
         prev = n_commit;
         if (c->profile) {
@@ -644,6 +652,7 @@ static int latched(tsim_ctx *c)
     if (st & ST_NUMERIC) return fail(TSIM_ERR_NUMERIC, "non-finite state or J <= 0 (instance " + std::to_string(first) + ")");
     if (st & ST_DOMAIN) return fail(TSIM_ERR_DOMAIN, "a particle left the node box (instance " + std::to_string(first) + ")");
     if (st & ST_CAPACITY) return fail(TSIM_ERR_CAPACITY, "a cell block overflowed (instance " + std::to_string(first) + ")");
+    if (st & ST_TIMEOUT) return fail(TSIM_ERR_TIMEOUT, "a device wait gave up (instance " + std::to_string(first) + ")");
     return TSIM_OK;
 }
 

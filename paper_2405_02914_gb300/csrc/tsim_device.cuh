@@ -15,10 +15,13 @@
 namespace tsim {
 
 constexpr int BLK = 4;               // cells per cell-block edge
-constexpr int CAP = 1024;            // particle slots per cell block
-constexpr int NT = 128;              // threads of the fused transfer kernel
+constexpr int CAP = 768;             // particle slots per cell block (1.5x the 512 of 8 ppc)
+constexpr int NT = 128;              // threads of the fused transfer kernel (2 per cell)
 constexpr int GV = 6;                // G2P node window edge (BLK + 2)
 constexpr int GA = 8;                // P2G node window edge (BLK + 4: +-1 cell of motion)
+constexpr int GAZ = 68;              // z stride of the P2G window (64 + 4: conflict-free banks)
+constexpr int GAN = GAZ * GA;        // floats per P2G window channel
+constexpr int NCELL = BLK * BLK * BLK;
 constexpr int MAX_KF = 64;
 constexpr int LOGN = 4096;
 
@@ -26,7 +29,7 @@ constexpr uint32_t TAG_BOTTOM = 0x80000000u;
 constexpr uint32_t TAG_TOP = 0x40000000u;
 constexpr uint32_t ID_MASK = 0x1FFFFFFFu;
 
-enum : uint32_t { ST_NUMERIC = 1u, ST_DOMAIN = 2u, ST_CAPACITY = 4u };
+enum : uint32_t { ST_NUMERIC = 1u, ST_DOMAIN = 2u, ST_CAPACITY = 4u, ST_TIMEOUT = 8u };
 enum { K_NONE = -1, K_SPHERE = 0, K_CYLINDER = 1, K_BOX = 2, K_PRISM = 3, K_PERLIN = 4 };
 enum { BASE_FIXED = 0, BASE_SLIP = 1, BASE_FREE = 2 };
 
@@ -59,7 +62,7 @@ struct InstState {                 // mutable per instance
     Pose pose;
     float xe[3];
     int e_id;
-    int phase;                     // 0 iterating, 1 commits this pass, 2 done this substep
+    int phase;                     // 0 iterating, 1 accepted: the commit transfer moves x and F
     int pass;
     unsigned int status;
     int dirty;

@@ -151,9 +151,7 @@ __global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle
     for (int inst = threadIdx.x; inst < d.n_inst; inst += blockDim.x) {
         InstState *S = d.ist + inst;
         const Inst &I = d.inst[inst];
-        const int ph = S->phase;
-        if (ph == 1) { S->phase = 2; continue; }
-        if (ph != 0) continue;
+        if (S->phase != 0) continue;        // committing or done: the commit transfer follows the loop
         bool accept = true;
         const Pose &P = S->pose;
         if (I.ind_kind != K_NONE && S->e_id >= 0) {
@@ -217,14 +215,159 @@ __global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle
 
 enum { MODE_PROLOGUE = 0, MODE_ITER = 1, MODE_COMMIT = 2 };
 
-template <int MODE>
-__global__ void __launch_bounds__(NT) k_transfer(Dev d, int block_offset)
+// Shared memory of one cell block (dynamic, ~61 KB).
+struct TransferSmem {
+    // staged x (0..2), F (3..11) and tag bits (12) of the block's particles (TMA);
+    // phase 1 overwrites a particle's entries with its P2G coefficients:
+    // Q (0..8), m v (9..11), fractional offset f of the new position (12..14)
+    float P[15][CAP];
+    float4 V[GV * GV * GV];        // grid velocities of the G2P window
+    float A[4][GAN];               // P2G window accumulator (M, MG)
+    unsigned short idx[CAP];       // particle order sorted by cell
+    unsigned char cell[CAP];       // cell of each particle (255: handled by atomics / invalid)
+    int ccount[NCELL], coff[NCELL], ccur[NCELL];
+    unsigned long long bar;        // mbarrier of the bulk copies
+    unsigned long long key[NT / 32];
+    float pos[NT / 32][3];
+    float tip[3];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// packed FP32 pairs (one Blackwell instruction per pair)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// G2P of one particle from the block's velocity window (Eqs. 6-7), factorised
+// over the tensor-product weights: per (i, j) row the k-sums, per i the
+// j-sums, then the i-sum; d = x_i - x_p in cells.  Returns v and D = sum w V d^T.
+__device__ __forceinline__ void g2p_window(const float4 *__restrict__ Vw, int cx, int cy, int cz,
+                                           const float w[3][3], const float f[3], float v[3], float D[9])
 {
-    __shared__ float4 sV[GV * GV * GV];
-    __shared__ float sA[4][GA * GA * GA];
-    __shared__ unsigned long long s_key[NT / 32];
-    __shared__ float s_pos[NT / 32][3];
-    __shared__ float s_tip[3];
+    float2 wx[3], wy[3], wz[3], ex[3], ey[3], ez[3];
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        wx[o] = dup2(w[0][o]); ex[o] = dup2(w[0][o] * ((float)o - f[0]));
+        wy[o] = dup2(w[1][o]); ey[o] = dup2(w[1][o] * ((float)o - f[1]));
+        wz[o] = dup2(w[2][o]); ez[o] = dup2(w[2][o] * ((float)o - f[2]));
+    }
+    const float2 z2 = make_float2(0.f, 0.f);
+    float2 vxy = z2, vz = z2, Dxxy = z2, Dxz = z2, Dyxy = z2, Dyz = z2, Dzxy = z2, Dzz = z2;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float2 Uxy = z2, Uz = z2, Uyxy = z2, Uyz = z2, Uzxy = z2, Uzz = z2;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float2 Txy = z2, Tz = z2, Tzxy = z2, Tzz = z2;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float4 V = Vw[((cz + k) * GV + (cy + j)) * GV + (cx + i)];
+                const float2 Vxy = make_float2(V.x, V.y), Vz = make_float2(V.z, V.w);
+                Txy = ffma2(wz[k], Vxy, Txy);
+                Tz = ffma2(wz[k], Vz, Tz);
+                Tzxy = ffma2(ez[k], Vxy, Tzxy);
+                Tzz = ffma2(ez[k], Vz, Tzz);
+            }
+            Uxy = ffma2(wy[j], Txy, Uxy);
+            Uz = ffma2(wy[j], Tz, Uz);
+            Uyxy = ffma2(ey[j], Txy, Uyxy);
+            Uyz = ffma2(ey[j], Tz, Uyz);
+            Uzxy = ffma2(wy[j], Tzxy, Uzxy);
+            Uzz = ffma2(wy[j], Tzz, Uzz);
+        }
+        vxy = ffma2(wx[i], Uxy, vxy);
+        vz = ffma2(wx[i], Uz, vz);
+        Dxxy = ffma2(ex[i], Uxy, Dxxy);
+        Dxz = ffma2(ex[i], Uz, Dxz);
+        Dyxy = ffma2(wx[i], Uyxy, Dyxy);
+        Dyz = ffma2(wx[i], Uyz, Dyz);
+        Dzxy = ffma2(wx[i], Uzxy, Dzxy);
+        Dzz = ffma2(wx[i], Uzz, Dzz);
+    }
+    v[0] = vxy.x; v[1] = vxy.y; v[2] = vz.x;
+    // D[r][c] = sum w V_r d_c
+    D[0] = Dxxy.x; D[3] = Dxxy.y; D[6] = Dxz.x;
+    D[1] = Dyxy.x; D[4] = Dyxy.y; D[7] = Dyz.x;
+    D[2] = Dzxy.x; D[5] = Dzxy.y; D[8] = Dzz.x;
+}
+
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared (TMA); both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~1e6 polls (each poll may suspend briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 20); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// P2G of one particle into the block window with shared atomics (Eqs. 1-4);
+// used for particles whose stencil moved away from their cell.
+__device__ __noinline__ void p2g_atomic(float (*A)[GAN], int wx, int wy, int wz, const float w[3][3],
+                                        const float f[3], const float Q[9], const float mv[3], float mp)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) {
+                const float wt = w[0][i] * w[1][j] * w[2][k];
+                const float d0 = (float)i - f[0], d1 = (float)j - f[1], d2 = (float)k - f[2];
+                const int n = (wz + k) * GAZ + (wy + j) * GA + (wx + i);
+                atomicAdd(&A[0][n], wt * mp);
+                atomicAdd(&A[1][n], wt * (mv[0] + Q[0] * d0 + Q[1] * d1 + Q[2] * d2));
+                atomicAdd(&A[2][n], wt * (mv[1] + Q[3] * d0 + Q[4] * d1 + Q[5] * d2));
+                atomicAdd(&A[3][n], wt * (mv[2] + Q[6] * d0 + Q[7] * d1 + Q[8] * d2));
+            }
+}
+
+// One CTA per cell block of 4x4x4 cells:
+//   0. bulk-copy the block's x, F and tags into shared memory (TMA);
+//   1. particle-parallel: G2P from the shared velocity window (Eqs. 6-7), the
+//      F and x move on a commit pass (Eqs. 8-9), Kirchhoff stress (Eq. 4),
+//      re-binning and the write of the moved state; the particle's P2G
+//      coefficients replace its staged data, and a counting sort groups the
+//      particles by cell (the particles of a cell share one 27-node stencil);
+//   2. cell-parallel: two threads per cell accumulate the cell's 27-node
+//      stencil x 4 channels (Eqs. 1-4) in registers over its particles, then
+//      add it to the block's node window;
+//   3. the window goes to the grid with one vector atomic per touched node.
+template <int MODE>
+__global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TransferSmem &sm = *reinterpret_cast<TransferSmem *>(smem_raw);
 
     const int b = block_offset + blockIdx.x;
     const int inst = d.blk_inst[b];
@@ -245,91 +388,93 @@ __global__ void __launch_bounds__(NT) k_transfer(Dev d, int block_offset)
     const int count = min(d.cnt[par][b], CAP);          // an overflowed block was latched as an error
     if (count == 0 && !cands) return;
 
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int lb = b - I.block0;
     const int gx0 = (lb % I.nbx) * BLK, gy0 = ((lb / I.nbx) % I.nby) * BLK, gz0 = (lb / (I.nbx * I.nby)) * BLK;
-    const float dx = I.dx, inv_dx = I.inv_dx, dt = I.dt;
+    const float inv_dx = I.inv_dx, dt = I.dt;
+    const long long SS = d.S;
+    const long long slot0 = (long long)b * CAP;
 
+    // 0. bulk copies of the particle arrays (16-byte multiples; the slack is inside the block's slots)
+    if (tid == 0) {
+        mbar_init(&sm.bar, 1);
+        if (count > 0) {
+            const uint32_t bytes = (uint32_t)(((count + 3) & ~3) * 4);
+            mbar_expect_tx(&sm.bar, 13u * bytes);
+            const float *src = d.P[par];
+            for (int c = 0; c < 12; ++c) bulk_load(sm.P[c], src + c * SS + slot0, bytes, &sm.bar);
+            bulk_load(sm.P[12], d.T[par] + slot0, bytes, &sm.bar);
+        }
+        if (MODE == MODE_PROLOGUE) {
+            double t4[4], v4[4];
+            pose_tip(d.kf + (long long)inst * MAX_KF * 5, I.nkf, d.G->k_next, t4, v4, (double)dt);
+            sm.tip[0] = (float)t4[0]; sm.tip[1] = (float)t4[1]; sm.tip[2] = (float)t4[2];
+        } else {
+            sm.tip[0] = S->pose.tip_next[0]; sm.tip[1] = S->pose.tip_next[1]; sm.tip[2] = S->pose.tip_next[2];
+        }
+    }
     if (MODE != MODE_PROLOGUE) {
-        for (int t = threadIdx.x; t < GV * GV * GV; t += NT) {
+        for (int t = tid; t < GV * GV * GV; t += NT) {
             const int lx = t % GV, ly = (t / GV) % GV, lz = t / (GV * GV);
             const int ax = gx0 + lx, ay = gy0 + ly, az = gz0 + lz;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (ax < I.nx && ay < I.ny && az < I.nz) v = d.vel[node_of(I, ax, ay, az)];
-            sV[t] = v;
+            sm.V[t] = v;
         }
     }
-    for (int t = threadIdx.x; t < GA * GA * GA; t += NT) {
-        sA[0][t] = 0.f; sA[1][t] = 0.f; sA[2][t] = 0.f; sA[3][t] = 0.f;
+    for (int t = tid; t < GAN; t += NT) {
+        sm.A[0][t] = 0.f; sm.A[1][t] = 0.f; sm.A[2][t] = 0.f; sm.A[3][t] = 0.f;
     }
-    if (threadIdx.x == 0) {
-        if (MODE == MODE_PROLOGUE) {
-            double t4[4], v4[4];
-            pose_tip(d.kf + (long long)inst * MAX_KF * 5, I.nkf, d.G->k_next, t4, v4, (double)dt);
-            s_tip[0] = (float)t4[0]; s_tip[1] = (float)t4[1]; s_tip[2] = (float)t4[2];
-        } else {
-            s_tip[0] = S->pose.tip_next[0]; s_tip[1] = S->pose.tip_next[1]; s_tip[2] = S->pose.tip_next[2];
-        }
-    }
+    if (tid < NCELL) { sm.ccount[tid] = 0; sm.ccur[tid] = 0; }
     __syncthreads();
+    const bool got = count == 0 || mbar_wait_bounded(&sm.bar, 0);
+    if (!__syncthreads_and(got)) {
+        if (tid == 0) atomic_or_status(S, ST_TIMEOUT);
+        return;
+    }
 
-    const long long SS = d.S;
-    const float *src = d.P[par];
-    const uint32_t *srcT = d.T[par];
+    // 1. particle-parallel pass
+    unsigned int err = 0;
+    const float tip0 = sm.tip[0], tip1 = sm.tip[1], tip2 = sm.tip[2];
     float *dst = d.P[par ^ 1];
     uint32_t *dstT = d.T[par ^ 1];
     int *cntDst = d.cnt[par ^ 1];
     const bool store_vc = moves && (d.G->k_cur + 1 == d.G->k_end);
-    const float tip0 = s_tip[0], tip1 = s_tip[1], tip2 = s_tip[2];
-    const int lane = threadIdx.x & 31;
     unsigned long long best = ~0ull;
     float bpos[3] = {0.f, 0.f, 0.f};
-    unsigned int err = 0;
-
     for (int r0 = 0; r0 < count; r0 += NT) {
-        const int r = r0 + threadIdx.x;
+        const int r = r0 + tid;
         bool valid = r < count;
-        const long long slot = (long long)b * CAP + r;
         float x[3], F[9], v[3] = {0.f, 0.f, 0.f}, C[9];
         uint32_t tag = 0;
+        int cl = 255;
         if (valid) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) x[c] = src[c * SS + slot];
+            for (int c = 0; c < 3; ++c) x[c] = sm.P[c][r];
 #pragma unroll
-            for (int c = 0; c < 9; ++c) F[c] = src[(3 + c) * SS + slot];
-            tag = srcT[slot];
-            if (MODE == MODE_PROLOGUE) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) v[c] = d.VC[c * SS + slot];
-#pragma unroll
-                for (int c = 0; c < 9; ++c) C[c] = d.VC[(3 + c) * SS + slot];
+            for (int c = 0; c < 9; ++c) F[c] = sm.P[3 + c][r];
+            tag = __float_as_uint(sm.P[12][r]);
+            float f[3], w[3][3];
+            int bx, by, bz;
+            bspline(x[0], inv_dx, bx, f[0], w[0]);
+            bspline(x[1], inv_dx, by, f[1], w[1]);
+            bspline(x[2], inv_dx, bz, f[2], w[2]);
+            const int lx = bx + I.ox - gx0, ly = by + I.oy - gy0, lz = bz + I.oz - gz0;
+            if (lx < 0 || ly < 0 || lz < 0 || lx >= BLK || ly >= BLK || lz >= BLK) {
+                err |= ST_DOMAIN;
+                valid = false;
             } else {
-                // G2P: v = sum w V (Eq. 6), C = 4/dx^2 sum w V (x_i - x_p)^T (Eq. 7)
-                int base[3];
-                float f[3], w[3][3];
+                cl = (lz * BLK + ly) * BLK + lx;
+                if (MODE == MODE_PROLOGUE) {
+                    const long long slot = slot0 + r;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) bspline(x[a], inv_dx, base[a], f[a], w[a]);
-                const int lx = base[0] + I.ox - gx0, ly = base[1] + I.oy - gy0, lz = base[2] + I.oz - gz0;
-                if (lx < 0 || ly < 0 || lz < 0 || lx >= BLK || ly >= BLK || lz >= BLK) {
-                    err |= ST_DOMAIN;
-                    valid = false;
+                    for (int c = 0; c < 3; ++c) v[c] = d.VC[c * SS + slot];
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) C[c] = d.VC[(3 + c) * SS + slot];
                 } else {
-#pragma unroll
-                    for (int c = 0; c < 9; ++c) C[c] = 0.f;
-#pragma unroll
-                    for (int i = 0; i < 3; ++i)
-#pragma unroll
-                        for (int j = 0; j < 3; ++j)
-#pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                const float4 Vn = sV[((lz + k) * GV + (ly + j)) * GV + (lx + i)];
-                                const float wt = w[0][i] * w[1][j] * w[2][k];
-                                const float d0 = ((float)i - f[0]), d1 = ((float)j - f[1]), d2 = ((float)k - f[2]);
-                                const float wv0 = wt * Vn.x, wv1 = wt * Vn.y, wv2 = wt * Vn.z;
-                                v[0] += wv0; v[1] += wv1; v[2] += wv2;
-                                C[0] += wv0 * d0; C[1] += wv0 * d1; C[2] += wv0 * d2;
-                                C[3] += wv1 * d0; C[4] += wv1 * d1; C[5] += wv1 * d2;
-                                C[6] += wv2 * d0; C[7] += wv2 * d1; C[8] += wv2 * d2;
-                            }
+                    // G2P: v = sum w V (Eq. 6), C = 4/dx^2 sum w V (x_i - x_p)^T (Eq. 7)
+                    g2p_window(sm.V, lx, ly, lz, w, f, v, C);
                     const float s4 = 4.f * inv_dx;   // (4/dx^2) * dx: d above is in cells
 #pragma unroll
                     for (int c = 0; c < 9; ++c) C[c] *= s4;
@@ -351,55 +496,54 @@ __global__ void __launch_bounds__(NT) k_transfer(Dev d, int block_offset)
 #pragma unroll
             for (int c = 0; c < 3; ++c) x[c] += dt * v[c];
         }
-        // stress (S_p of Eq. 4) of the state that enters P2G
-        float tau[9];
-        int nbase[3] = {0, 0, 0};
-        float nf[3] = {0.f, 0.f, 0.f}, nw[3][3];
+        int nb[3] = {0, 0, 0};
         if (valid) {
+            // stress (S_p of Eq. 4) and the P2G coefficients of the state that enters P2G
+            float tau[9];
             const float J = kirchhoff(F, I.mu, I.lam, tau);
             if (!(J > 0.f) || !isfinite(J) || !isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2])) {
                 err |= ST_NUMERIC;
                 valid = false;
-            }
-        }
-        if (valid) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) bspline(x[a], inv_dx, nbase[a], nf[a], nw[a]);
-            const int ax = nbase[0] + I.ox, ay = nbase[1] + I.oy, az = nbase[2] + I.oz;
-            const int wx = ax - (gx0 - 1), wy = ay - (gy0 - 1), wz = az - (gz0 - 1);
-            if (ax < 0 || ay < 0 || az < 0 || ax + 2 >= I.nx || ay + 2 >= I.ny || az + 2 >= I.nz ||
-                wx < 0 || wy < 0 || wz < 0 || wx + 2 >= GA || wy + 2 >= GA || wz + 2 >= GA) {
-                err |= ST_DOMAIN;
-                valid = false;
             } else {
-                // P2G: M += w m (Eq. 1); MG += w (m v + m C d) - 4 dt/dx^2 V0 w tau d (Eqs. 2-4)
-                float Q[9];
+                float nf[3], nw[3][3];
 #pragma unroll
-                for (int c = 0; c < 9; ++c) Q[c] = (I.mp * C[c] + I.kME * tau[c]) * dx;   // d below in cells
-                const float mv0 = I.mp * v[0], mv1 = I.mp * v[1], mv2 = I.mp * v[2];
+                for (int a = 0; a < 3; ++a) bspline(x[a], inv_dx, nb[a], nf[a], nw[a]);
+                nb[0] += I.ox; nb[1] += I.oy; nb[2] += I.oz;          // box index of the new base node
+                const int wx = nb[0] - (gx0 - 1), wy = nb[1] - (gy0 - 1), wz = nb[2] - (gz0 - 1);
+                if (nb[0] < 0 || nb[1] < 0 || nb[2] < 0 || nb[0] + 2 >= I.nx || nb[1] + 2 >= I.ny ||
+                    nb[2] + 2 >= I.nz || wx < 0 || wy < 0 || wz < 0 || wx + 2 >= GA || wy + 2 >= GA ||
+                    wz + 2 >= GA) {
+                    err |= ST_DOMAIN;
+                    valid = false;
+                } else {
+                    // P2G: M += w m (Eq. 1); MG += w (m v + m C d) - 4 dt/dx^2 V0 w tau d (Eqs. 2-4);
+                    // Q carries one cell of d so that d can be counted in cells
+                    float Q[9];
 #pragma unroll
-                for (int i = 0; i < 3; ++i)
+                    for (int c = 0; c < 9; ++c) Q[c] = (I.mp * C[c] + I.kME * tau[c]) * I.dx;
+                    const float mv[3] = {I.mp * v[0], I.mp * v[1], I.mp * v[2]};
+                    const bool stays = wx == (cl & 3) + 1 && wy == ((cl >> 2) & 3) + 1 && wz == (cl >> 4) + 1;
+                    if (stays) {
 #pragma unroll
-                    for (int j = 0; j < 3; ++j)
+                        for (int c = 0; c < 9; ++c) sm.P[c][r] = Q[c];
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            const float wt = nw[0][i] * nw[1][j] * nw[2][k];
-                            const float d0 = (float)i - nf[0], d1 = (float)j - nf[1], d2 = (float)k - nf[2];
-                            const int n = ((wz + k) * GA + (wy + j)) * GA + (wx + i);
-                            atomicAdd(&sA[0][n], wt * I.mp);
-                            atomicAdd(&sA[1][n], wt * (mv0 + Q[0] * d0 + Q[1] * d1 + Q[2] * d2));
-                            atomicAdd(&sA[2][n], wt * (mv1 + Q[3] * d0 + Q[4] * d1 + Q[5] * d2));
-                            atomicAdd(&sA[3][n], wt * (mv2 + Q[6] * d0 + Q[7] * d1 + Q[8] * d2));
-                        }
+                        for (int c = 0; c < 3; ++c) sm.P[9 + c][r] = mv[c];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) sm.P[12 + c][r] = nf[c];
+                    } else {
+                        p2g_atomic(sm.A, wx, wy, wz, nw, nf, Q, mv, I.mp);
+                        cl = 255;
+                    }
+                }
             }
         }
+        if (!valid) cl = 255;
+        if (r < count) sm.cell[r] = (unsigned char)cl;
+        if (cl != 255) atomicAdd(&sm.ccount[cl], 1);
         if (moves) {
             // re-bin into the cell block of the new position: warp-aggregated slot claims
             unsigned int key = 0xffffffffu;
-            if (valid) {
-                const int ax = nbase[0] + I.ox, ay = nbase[1] + I.oy, az = nbase[2] + I.oz;
-                key = (unsigned int)(I.block0 + ((az / BLK) * I.nby + (ay / BLK)) * I.nbx + (ax / BLK));
-            }
+            if (valid) key = (unsigned int)(I.block0 + ((nb[2] / BLK) * I.nby + (nb[1] / BLK)) * I.nbx + (nb[0] / BLK));
             const unsigned int peers = __match_any_sync(0xffffffffu, key);
             const int leader = __ffs(peers) - 1;
             const int rank = __popc(peers & ((1u << lane) - 1u));
@@ -435,13 +579,106 @@ __global__ void __launch_bounds__(NT) k_transfer(Dev d, int block_offset)
     }
     if (err) atomic_or_status(S, err);
     __syncthreads();
-    // flush the block-local grid window: one vector atomic per touched node
-    for (int t = threadIdx.x; t < GA * GA * GA; t += NT) {
-        const float m = sA[0][t];
+    if (tid < 32) {                                  // exclusive scan of the 64 cell counts
+        const int a0 = sm.ccount[2 * tid], a1 = sm.ccount[2 * tid + 1];
+        int incl = a0 + a1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += y;
+        }
+        const int excl = incl - a0 - a1;
+        sm.coff[2 * tid] = excl;
+        sm.coff[2 * tid + 1] = excl + a0;
+    }
+    __syncthreads();
+    for (int r = tid; r < count; r += NT) {
+        const int c = sm.cell[r];
+        if (c != 255) sm.idx[sm.coff[c] + atomicAdd(&sm.ccur[c], 1)] = (unsigned short)r;
+    }
+    __syncthreads();
+
+    // 2. cell-parallel P2G: two threads per cell (each half of its particles),
+    //    the lanes of a warp on 32 different cells, 27 nodes x 4 channels in registers
+    {
+        const int cl = tid & (NCELL - 1), half = tid >> 6;
+        const int clx = cl & 3, cly = (cl >> 2) & 3, clz = cl >> 4;
+        const int ncl = sm.ccount[cl], off = sm.coff[cl];
+        const int my_n = (ncl - half + 1) >> 1;
+        const float2 z2 = make_float2(0.f, 0.f);
+        float2 acca[27], accb[27];
+#pragma unroll
+        for (int o = 0; o < 27; ++o) { acca[o] = z2; accb[o] = z2; }
+        for (int it = 0; it < my_n; ++it) {
+            const int r = sm.idx[off + half + 2 * it];
+            float Q[9], mv[3], f[3], w[3][3];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) Q[c] = sm.P[c][r];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) mv[c] = sm.P[9 + c][r];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                f[c] = sm.P[12 + c][r];
+                const float a = 1.5f - f[c], bb = f[c] - 1.f, cc = f[c] - 0.5f;
+                w[c][0] = 0.5f * a * a; w[c][1] = 0.75f - bb * bb; w[c][2] = 0.5f * cc * cc;
+            }
+            float2 Aa[3], Ab[3], Ya[3], Yb[3], Za[3], Zb[3], wy2[3], wz2[3];
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+                const float d0 = (float)o - f[0], d1 = (float)o - f[1], d2 = (float)o - f[2];
+                Aa[o] = make_float2(1.f, mv[0] + Q[0] * d0);
+                Ab[o] = make_float2(mv[1] + Q[3] * d0, mv[2] + Q[6] * d0);
+                Ya[o] = make_float2(0.f, Q[1] * d1);
+                Yb[o] = make_float2(Q[4] * d1, Q[7] * d1);
+                Za[o] = make_float2(0.f, Q[2] * d2);
+                Zb[o] = make_float2(Q[5] * d2, Q[8] * d2);
+                wy2[o] = dup2(w[1][o]);
+                wz2[o] = dup2(w[2][o]);
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float2 wx2 = dup2(w[0][i]);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const float2 wij = fmul2(wx2, wy2[j]);
+                    const float2 Aij = fadd2(Aa[i], Ya[j]), Bij = fadd2(Ab[i], Yb[j]);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const int o = (i * 3 + j) * 3 + k;
+                        const float2 w2 = fmul2(wij, wz2[k]);
+                        acca[o] = ffma2(w2, fadd2(Aij, Za[k]), acca[o]);
+                        accb[o] = ffma2(w2, fadd2(Bij, Zb[k]), accb[o]);
+                    }
+                }
+            }
+        }
+        if (my_n > 0) {
+            const float mp = I.mp;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const int o = (i * 3 + j) * 3 + k;
+                        const int n = (clz + 1 + k) * GAZ + (cly + 1 + j) * GA + (clx + 1 + i);
+                        atomicAdd(&sm.A[0][n], acca[o].x * mp);
+                        atomicAdd(&sm.A[1][n], acca[o].y);
+                        atomicAdd(&sm.A[2][n], accb[o].x);
+                        atomicAdd(&sm.A[3][n], accb[o].y);
+                    }
+        }
+    }
+    __syncthreads();
+    // 3. block window -> grid: one vector atomic per touched node
+    for (int t = tid; t < GA * GA * GA; t += NT) {
+        const int lx = t % GA, ly = (t / GA) % GA, lz = t / (GA * GA);
+        const int n = lz * GAZ + ly * GA + lx;
+        const float m = sm.A[0][n];
         if (m != 0.f) {
-            const int ax = gx0 - 1 + t % GA, ay = gy0 - 1 + (t / GA) % GA, az = gz0 - 1 + t / (GA * GA);
+            const int ax = gx0 - 1 + lx, ay = gy0 - 1 + ly, az = gz0 - 1 + lz;
             if (ax >= 0 && ay >= 0 && az >= 0 && ax < I.nx && ay < I.ny && az < I.nz)
-                atomicAdd(&d.acc[node_of(I, ax, ay, az)], make_float4(m, sA[1][t], sA[2][t], sA[3][t]));
+                atomicAdd(&d.acc[node_of(I, ax, ay, az)], make_float4(m, sm.A[1][n], sm.A[2][n], sm.A[3][n]));
         }
     }
     if (cands) {
@@ -454,23 +691,25 @@ __global__ void __launch_bounds__(NT) k_transfer(Dev d, int block_offset)
             if (ok < best) { best = ok; bpos[0] = o0; bpos[1] = o1; bpos[2] = o2; }
         }
         if (lane == 0) {
-            s_key[threadIdx.x >> 5] = best;
-            s_pos[threadIdx.x >> 5][0] = bpos[0];
-            s_pos[threadIdx.x >> 5][1] = bpos[1];
-            s_pos[threadIdx.x >> 5][2] = bpos[2];
+            sm.key[tid >> 5] = best;
+            sm.pos[tid >> 5][0] = bpos[0];
+            sm.pos[tid >> 5][1] = bpos[1];
+            sm.pos[tid >> 5][2] = bpos[2];
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             int wbest = 0;
             for (int a = 1; a < NT / 32; ++a)
-                if (s_key[a] < s_key[wbest]) wbest = a;
+                if (sm.key[a] < sm.key[wbest]) wbest = a;
             Cand c;
-            c.key = s_key[wbest];
-            c.x = s_pos[wbest][0]; c.y = s_pos[wbest][1]; c.z = s_pos[wbest][2]; c.pad = 0.f;
+            c.key = sm.key[wbest];
+            c.x = sm.pos[wbest][0]; c.y = sm.pos[wbest][1]; c.z = sm.pos[wbest][2]; c.pad = 0.f;
             d.cand[b] = c;
         }
     }
 }
+
+size_t transfer_smem_bytes() { return sizeof(TransferSmem); }
 
 // ---------------------------------------------------------------- staging <-> slots
 
@@ -637,12 +876,24 @@ void launch_check(const Dev &d, cudaGraphConditionalHandle h, int use_cond, cuda
     k_check<<<1, 256, 0, s>>>(d, h, use_cond);
 }
 
+cudaError_t setup_kernels()
+{
+    const int bytes = (int)sizeof(TransferSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_transfer<MODE_PROLOGUE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_transfer<MODE_ITER>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_transfer<MODE_COMMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
 void launch_transfer(const Dev &d, int mode, int block_offset, int nblocks, cudaStream_t s)
 {
     if (nblocks <= 0) return;
-    if (mode == MODE_PROLOGUE) k_transfer<MODE_PROLOGUE><<<nblocks, NT, 0, s>>>(d, block_offset);
-    else if (mode == MODE_ITER) k_transfer<MODE_ITER><<<nblocks, NT, 0, s>>>(d, block_offset);
-    else k_transfer<MODE_COMMIT><<<nblocks, NT, 0, s>>>(d, block_offset);
+    const size_t sh = sizeof(TransferSmem);
+    if (mode == MODE_PROLOGUE) k_transfer<MODE_PROLOGUE><<<nblocks, NT, sh, s>>>(d, block_offset);
+    else if (mode == MODE_ITER) k_transfer<MODE_ITER><<<nblocks, NT, sh, s>>>(d, block_offset);
+    else k_transfer<MODE_COMMIT><<<nblocks, NT, sh, s>>>(d, block_offset);
 }
 
 void launch_bin_staged(const Dev &d, int inst, int n, int par, cudaStream_t s)

@@ -17,7 +17,8 @@ from . import build as _build
 
 TSIM_OK = 0
 ERRORS = {1: "TSIM_ERR_INVALID_ARG", 2: "TSIM_ERR_OOM", 3: "TSIM_ERR_CUDA", 4: "TSIM_ERR_NUMERIC",
-          5: "TSIM_ERR_DOMAIN", 6: "TSIM_ERR_CAPACITY", 7: "TSIM_ERR_STATE"}
+          5: "TSIM_ERR_DOMAIN", 6: "TSIM_ERR_CAPACITY", 7: "TSIM_ERR_STATE",
+          8: "TSIM_ERR_TIMEOUT"}
 
 EXPORTS = ["tsim_create", "tsim_set_solver", "tsim_set_indenter", "tsim_set_trajectory",
            "tsim_write_particles", "tsim_set_substep", "tsim_step", "tsim_read_particles",
