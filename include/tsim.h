@@ -224,6 +224,36 @@ int tsim_use_graph(tsim_ctx *ctx, int enable);
 int tsim_profile(tsim_ctx *ctx, int enable);
 int tsim_kernel_time(tsim_ctx *ctx, int64_t *launches, double *total_ms);
 
+/* ---- Allocation-free particle-to-grid transfer --------------------------
+ * Not a part of the paper's method: the paper has no counterpart.  It serves
+ * callers that cannot allocate device memory -- a plug-in whose host
+ * application owns all device memory through its own pool, a real-time loop
+ * that must not touch the allocator once running, a process with a memory
+ * budget fixed at start-up.  It computes the same transfer as the P2G of a
+ * context (mass and momentum of Eqs. 1-4, as tsim_read_grid returns it) for
+ * a particle state and a grid the caller owns, using only a fixed scratch
+ * array of TSIM_NOALLOC_SCRATCH_BYTES bytes that the library reserves
+ * statically on every GPU that loads it (held until the process exits).
+ *
+ * gel, mat: host descriptors (node box a multiple of 4 in every direction,
+ * at most TSIM_NOALLOC_MAX_BLOCKS 4x4x4 cell blocks); dt: substep of the
+ * stress impulse of Eq. 4; x[n*3], v[n*3], C[n*9], F[n*9]: device arrays in
+ * the layout of tsim_write_particles, 1 <= n <= TSIM_NOALLOC_MAX_PARTICLES;
+ * grid[nx*ny*nz*4]: device output, 16-byte aligned, (M, MG) per node, x
+ * fastest (overwritten); stream: cudaStream_t or NULL.
+ * Sizes beyond the maxima return TSIM_ERR_INVALID_ARG before any GPU work.
+ * Particles outside the node box give TSIM_ERR_DOMAIN, J <= 0 gives
+ * TSIM_ERR_NUMERIC.  The call waits for its work on the stream before it
+ * returns.  It never allocates: the first call on a device looks up the
+ * scratch address for that device (make that first call before any stream
+ * capture); every call shares the scratch and clears what must start at
+ * zero, so calls that overlap on the GPU race and must be serialised. */
+#define TSIM_NOALLOC_MAX_PARTICLES (1 << 20)
+#define TSIM_NOALLOC_MAX_BLOCKS (1 << 15)
+#define TSIM_NOALLOC_SCRATCH_BYTES (3 * 4 * TSIM_NOALLOC_MAX_BLOCKS + 4 * TSIM_NOALLOC_MAX_PARTICLES + 256)
+int tsim_p2g_noalloc(const tsim_gel_desc *gel, const tsim_material *mat, float dt, const float *x,
+                     const float *v, const float *C, const float *F, int n, float *grid, void *stream);
+
 /* Reason for the last failure on this thread (never NULL). */
 const char *tsim_last_error(void);
 

@@ -73,6 +73,9 @@ static const int MARK_MAX = 4096;
 
 extern "C" const char *tsim_last_error(void) { return g_err.c_str(); }
 
+// used by the allocation-free entry point (tsim_noalloc.cu) to report through tsim_last_error
+void tsim_record_error(const std::string &msg) { g_err = msg; }
+
 static void free_all(tsim_ctx *c)
 {
     Dev &d = c->d;

@@ -24,7 +24,7 @@ EXPORTS = ["tsim_create", "tsim_set_solver", "tsim_set_indenter", "tsim_set_traj
            "tsim_write_particles", "tsim_set_substep", "tsim_step", "tsim_read_particles",
            "tsim_read_grid", "tsim_read_surface", "tsim_read_markers", "tsim_read_log", "tsim_sync",
            "tsim_stats", "tsim_use_graph", "tsim_profile", "tsim_kernel_time", "tsim_last_error",
-           "tsim_destroy"]
+           "tsim_destroy", "tsim_p2g_noalloc"]
 
 
 class TsimError(RuntimeError):
@@ -92,6 +92,8 @@ def load():
             "tsim_kernel_time": (C.c_int, [vp, P(C.c_int64), P(C.c_double)]),
             "tsim_last_error": (C.c_char_p, []),
             "tsim_destroy": (None, [vp]),
+            "tsim_p2g_noalloc": (C.c_int, [P(GelDesc), P(MaterialDesc), C.c_float, vp, vp, vp, vp, C.c_int,
+                                           vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

@@ -21,7 +21,7 @@ HEADER = os.path.join(ROOT, "include", "tsim.h")
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(tsim_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(tsim_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_builds_and_loads():
@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol():
     names = _declared()
     assert len(names) >= 19
     out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True, check=True).stdout
-    exported = set(re.findall(r"\bT (tsim_[a-z_]+)$", out, flags=re.M))
+    exported = set(re.findall(r"\bT (tsim_[a-z0-9_]+)$", out, flags=re.M))
     missing = [n for n in names if n not in exported]
     assert not missing, missing
     assert set(names) == set(tsim.EXPORTS)
