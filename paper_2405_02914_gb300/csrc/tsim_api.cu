@@ -79,7 +79,7 @@ void tsim_record_error(const std::string &msg) { g_err = msg; }
 static void free_all(tsim_ctx *c)
 {
     Dev &d = c->d;
-    void *ptrs[] = {d.P[0], d.P[1], d.T[0], d.T[1], d.cnt[0], d.cnt[1], d.VC, d.acc, d.vel, d.cand,
+    void *ptrs[] = {d.P[0], d.P[1], d.T[0], d.T[1], d.cnt[0], d.cnt[1], d.VC, d.acc, d.vel,
                     d.blk_inst, d.inst, d.ist, d.G, (void *)d.kf, (void *)d.perm, d.log,
                     d.sx, d.sv, d.sC, d.sF, d.stag, c->ro, c->ids, c->pick};
     for (void *p : ptrs)
@@ -201,7 +201,7 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
         {(void **)&d.T[0], S * sizeof(uint32_t)},         {(void **)&d.T[1], S * sizeof(uint32_t)},
         {(void **)&d.cnt[0], blocks * sizeof(int)},       {(void **)&d.cnt[1], blocks * sizeof(int)},
         {(void **)&d.VC, S * 12 * sizeof(float)},         {(void **)&d.acc, nodes * sizeof(float4)},
-        {(void **)&d.vel, nodes * sizeof(float4)},        {(void **)&d.cand, blocks * sizeof(Cand)},
+        {(void **)&d.vel, nodes * sizeof(float4)},
         {(void **)&d.blk_inst, blocks * sizeof(int)},     {(void **)&d.inst, n_inst * sizeof(Inst)},
         {(void **)&d.ist, n_inst * sizeof(InstState)},    {(void **)&d.G, sizeof(Global)},
         {(void **)&d.kf, n_inst * MAX_KF * 5 * sizeof(float)},
@@ -388,6 +388,7 @@ static int run_prologue(tsim_ctx *c, int inst)
 {
     const Inst &I = c->hinst[inst];
     CU(cudaMemsetAsync(c->d.acc + I.node0, 0, sizeof(float4) * (size_t)I.nx * I.ny * I.nz, c->stream));
+    CU(cudaMemsetAsync(&c->d.ist[inst].e_key, 0xff, sizeof(unsigned long long), c->stream));
     int rc = set_dirty(c, inst, 1);
     if (rc) return rc;
     launch_transfer(c->d, MODE_PROLOGUE_, I.block0, I.nblocks, c->stream);
@@ -507,8 +508,8 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
         void *a_chk[] = {&d, &h, &use1};
         void *a_tr[] = {&d, &zero};
         cudaGraphNode_t n_r0, n_grid, n_chk, n_while, n_ev0 = nullptr, n_commit, n_ev1;
-        rc = add_kernel(g, &n_r0, prev ? &prev : nullptr, prev ? 1 : 0, fn_round_begin(), dim3(c->n_inst), dim3(256),
-                        a_r0);
+        rc = add_kernel(g, &n_r0, prev ? &prev : nullptr, prev ? 1 : 0, fn_round_begin(),
+                        dim3((c->n_inst + 127) / 128), dim3(128), a_r0);
         if (rc) break;
         rc = add_kernel(g, &n_grid, &n_r0, 1, fn_grid(), grid_grid, grid_blk, a_grid);
         if (rc) break;

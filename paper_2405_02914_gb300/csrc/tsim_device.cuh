@@ -60,6 +60,7 @@ struct Pose {
 
 struct InstState {                 // mutable per instance
     Pose pose;
+    unsigned long long e_key;      // nearest particle to the next tip: (squared-distance bits << 32) | slot
     float xe[3];
     int e_id;
     int phase;                     // 0 iterating, 1 accepted: the commit transfer moves x and F
@@ -75,11 +76,6 @@ struct Global {
     int par_next, par_cur;
 };
 
-struct __align__(16) Cand {        // per-block nearest-particle candidate for x_e
-    unsigned long long key;        // (float bits of squared distance << 32) | id
-    float x, y, z, pad;
-};
-
 struct Dev {                       // device pointers (passed by value to kernels)
     float *P[2];
     uint32_t *T[2];
@@ -87,7 +83,6 @@ struct Dev {                       // device pointers (passed by value to kernel
     float *VC;
     long long S;                   // slots per parity and component
     float4 *acc, *vel;
-    Cand *cand;
     int *blk_inst;
     Inst *inst;
     InstState *ist;

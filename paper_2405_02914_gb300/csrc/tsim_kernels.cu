@@ -31,51 +31,34 @@ __device__ __forceinline__ long long node_of(const Inst &I, int ax, int ay, int 
 
 // ---------------------------------------------------------------- round begin
 
-// One CTA per instance: pose of substep k (and the tip at k+1), pass state
-// reset, and x_e of Algorithm 1 -- the particle nearest to the tip x_o -- from
-// the per-block candidates written by the previous commit (or prologue).
+// One thread per instance: pose of substep k (and the tip at k+1), pass
+// state reset, and x_e of Algorithm 1 -- the particle nearest to the tip x_o
+// -- from the key that the previous commit (or prologue) left behind:
+// (squared-distance bits << 32) | slot of that particle in the current state.
 // Nothing in this kernel writes the global substep counters.
-__global__ void __launch_bounds__(256) k_round_begin(Dev d)
+__global__ void k_round_begin(Dev d)
 {
-    const int inst = blockIdx.x;
+    const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+    if (inst >= d.n_inst) return;
     InstState *S = d.ist + inst;
     const Inst &I = d.inst[inst];
-    __shared__ unsigned long long s_key[8];
-    __shared__ float s_pos[8][3];
     const long long k = d.G->k_next;
-    if (threadIdx.x == 0) {
-        Pose P;
-        pose_eval(I, d.kf + (long long)inst * MAX_KF * 5, k, P);
-        S->pose = P;
-        S->phase = 0;
-        S->pass = 0;
-    }
-    unsigned long long bk = ~0ull;
-    float bp[3] = {0.f, 0.f, 0.f};
-    for (int b = threadIdx.x; b < I.nblocks; b += blockDim.x) {
-        const Cand c = d.cand[I.block0 + b];
-        if (c.key < bk) { bk = c.key; bp[0] = c.x; bp[1] = c.y; bp[2] = c.z; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ok = __shfl_down_sync(0xffffffffu, bk, o);
-        const float o0 = __shfl_down_sync(0xffffffffu, bp[0], o);
-        const float o1 = __shfl_down_sync(0xffffffffu, bp[1], o);
-        const float o2 = __shfl_down_sync(0xffffffffu, bp[2], o);
-        if (ok < bk) { bk = ok; bp[0] = o0; bp[1] = o1; bp[2] = o2; }
-    }
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        s_key[w] = bk;
-        s_pos[w][0] = bp[0]; s_pos[w][1] = bp[1]; s_pos[w][2] = bp[2];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int wb = 0;
-        for (int a = 1; a < (int)(blockDim.x >> 5); ++a)
-            if (s_key[a] < s_key[wb]) wb = a;
-        S->e_id = s_key[wb] == ~0ull ? -1 : (int)(s_key[wb] & 0xffffffffull);
-        S->xe[0] = s_pos[wb][0]; S->xe[1] = s_pos[wb][1]; S->xe[2] = s_pos[wb][2];
+    const int par = d.G->par_next;
+    Pose P;
+    pose_eval(I, d.kf + (long long)inst * MAX_KF * 5, k, P);
+    S->pose = P;
+    S->phase = 0;
+    S->pass = 0;
+    const unsigned long long key = S->e_key;
+    S->e_key = ~0ull;                              // the commit of this substep fills it again
+    if (key == ~0ull) {
+        S->e_id = -1;
+    } else {
+        const long long slot = (long long)(key & 0xffffffffull);
+        S->xe[0] = d.P[par][slot];
+        S->xe[1] = d.P[par][d.S + slot];
+        S->xe[2] = d.P[par][2 * d.S + slot];
+        S->e_id = (int)(d.T[par][slot] & ID_MASK);
     }
 }
 
@@ -228,8 +211,8 @@ struct TransferSmem {
     int ccount[NCELL], coff[NCELL], ccur[NCELL];
     unsigned long long bar;        // mbarrier of the bulk copies
     unsigned long long key[NT / 32];
-    float pos[NT / 32][3];
     float tip[3];
+    Inst inst;                     // the instance constants, copied once per CTA
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -361,7 +344,7 @@ __device__ __noinline__ void p2g_atomic(float (*A)[GAN], int wx, int wy, int wz,
 //      particles by cell (the particles of a cell share one 27-node stencil);
 //   2. cell-parallel: two threads per cell accumulate the cell's 27-node
 //      stencil x 4 channels (Eqs. 1-4) in registers over its particles, then
-//      add it to the block's node window;
+//      add it to the block's node window in 27 conflict-free offset rounds;
 //   3. the window goes to the grid with one vector atomic per touched node.
 template <int MODE>
 __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
@@ -384,17 +367,16 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
     }
     const bool moves = MODE == MODE_COMMIT;
     const bool cands = MODE != MODE_ITER;
-    const Inst &I = d.inst[inst];
     const int count = min(d.cnt[par][b], CAP);          // an overflowed block was latched as an error
     if (count == 0 && !cands) return;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int lb = b - I.block0;
-    const int gx0 = (lb % I.nbx) * BLK, gy0 = ((lb / I.nbx) % I.nby) * BLK, gz0 = (lb / (I.nbx * I.nby)) * BLK;
-    const float inv_dx = I.inv_dx, dt = I.dt;
     const long long SS = d.S;
     const long long slot0 = (long long)b * CAP;
+    static_assert(sizeof(Inst) % 4 == 0 && sizeof(Inst) / 4 <= NT, "Inst is copied one word per thread");
+    if (tid < (int)(sizeof(Inst) / 4))
+        reinterpret_cast<int *>(&sm.inst)[tid] = reinterpret_cast<const int *>(d.inst + inst)[tid];
 
     // 0. bulk copies of the particle arrays (16-byte multiples; the slack is inside the block's slots)
     if (tid == 0) {
@@ -408,12 +390,22 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
         }
         if (MODE == MODE_PROLOGUE) {
             double t4[4], v4[4];
-            pose_tip(d.kf + (long long)inst * MAX_KF * 5, I.nkf, d.G->k_next, t4, v4, (double)dt);
+            const Inst &Ig = d.inst[inst];
+            pose_tip(d.kf + (long long)inst * MAX_KF * 5, Ig.nkf, d.G->k_next, t4, v4, (double)Ig.dt);
             sm.tip[0] = (float)t4[0]; sm.tip[1] = (float)t4[1]; sm.tip[2] = (float)t4[2];
         } else {
             sm.tip[0] = S->pose.tip_next[0]; sm.tip[1] = S->pose.tip_next[1]; sm.tip[2] = S->pose.tip_next[2];
         }
     }
+    for (int t = tid; t < GAN; t += NT) {
+        sm.A[0][t] = 0.f; sm.A[1][t] = 0.f; sm.A[2][t] = 0.f; sm.A[3][t] = 0.f;
+    }
+    if (tid < NCELL) { sm.ccount[tid] = 0; sm.ccur[tid] = 0; }
+    __syncthreads();
+    const Inst &I = sm.inst;
+    const int lb = b - I.block0;
+    const int gx0 = (lb % I.nbx) * BLK, gy0 = ((lb / I.nbx) % I.nby) * BLK, gz0 = (lb / (I.nbx * I.nby)) * BLK;
+    const float inv_dx = I.inv_dx, dt = I.dt;
     if (MODE != MODE_PROLOGUE) {
         for (int t = tid; t < GV * GV * GV; t += NT) {
             const int lx = t % GV, ly = (t / GV) % GV, lz = t / (GV * GV);
@@ -423,11 +415,6 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
             sm.V[t] = v;
         }
     }
-    for (int t = tid; t < GAN; t += NT) {
-        sm.A[0][t] = 0.f; sm.A[1][t] = 0.f; sm.A[2][t] = 0.f; sm.A[3][t] = 0.f;
-    }
-    if (tid < NCELL) { sm.ccount[tid] = 0; sm.ccur[tid] = 0; }
-    __syncthreads();
     const bool got = count == 0 || mbar_wait_bounded(&sm.bar, 0);
     if (!__syncthreads_and(got)) {
         if (tid == 0) atomic_or_status(S, ST_TIMEOUT);
@@ -442,7 +429,6 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
     int *cntDst = d.cnt[par ^ 1];
     const bool store_vc = moves && (d.G->k_cur + 1 == d.G->k_end);
     unsigned long long best = ~0ull;
-    float bpos[3] = {0.f, 0.f, 0.f};
     for (int r0 = 0; r0 < count; r0 += NT) {
         const int r = r0 + tid;
         bool valid = r < count;
@@ -497,6 +483,7 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
             for (int c = 0; c < 3; ++c) x[c] += dt * v[c];
         }
         int nb[3] = {0, 0, 0};
+        long long cand_slot = moves ? -1 : slot0 + r;   // commit: set where the particle is written
         if (valid) {
             // stress (S_p of Eq. 4) and the P2G coefficients of the state that enters P2G
             float tau[9];
@@ -556,6 +543,7 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
                     err |= ST_CAPACITY;
                 } else {
                     const long long ds = (long long)key * CAP + rr;
+                    cand_slot = ds;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) dst[c * SS + ds] = x[c];
 #pragma unroll
@@ -570,11 +558,11 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
                 }
             }
         }
-        if (cands && valid) {
+        if (cands && valid && cand_slot >= 0) {
             const float e0 = x[0] - tip0, e1 = x[1] - tip1, e2 = x[2] - tip2;
             const float dd = e0 * e0 + e1 * e1 + e2 * e2;
-            const unsigned long long kk = ((unsigned long long)__float_as_uint(dd) << 32) | (tag & ID_MASK);
-            if (kk < best) { best = kk; bpos[0] = x[0]; bpos[1] = x[1]; bpos[2] = x[2]; }
+            const unsigned long long kk = ((unsigned long long)__float_as_uint(dd) << 32) | (unsigned int)cand_slot;
+            if (kk < best) best = kk;
         }
     }
     if (err) atomic_or_status(S, err);
@@ -598,10 +586,10 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
     }
     __syncthreads();
 
-    // 2. cell-parallel P2G: two threads per cell (each half of its particles),
-    //    the lanes of a warp on 32 different cells, 27 nodes x 4 channels in registers
+    // 2. cell-parallel P2G: two threads per cell (adjacent lanes, each half of
+    //    the cell's particles), 27 nodes x 4 channels in registers
     {
-        const int cl = tid & (NCELL - 1), half = tid >> 6;
+        const int cl = tid >> 1, half = tid & 1;
         const int clx = cl & 3, cly = (cl >> 2) & 3, clz = cl >> 4;
         const int ncl = sm.ccount[cl], off = sm.coff[cl];
         const int my_n = (ncl - half + 1) >> 1;
@@ -652,22 +640,38 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
                 }
             }
         }
-        if (my_n > 0) {
-            const float mp = I.mp;
+        // the two lanes of a cell swap halves so that the even lane holds the
+        // cell's (M, MG_x) and the odd lane its (MG_y, MG_z)
+        const float mp = I.mp;
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const int o = (i * 3 + j) * 3 + k;
-                        const int n = (clz + 1 + k) * GAZ + (cly + 1 + j) * GA + (clx + 1 + i);
-                        atomicAdd(&sm.A[0][n], acca[o].x * mp);
-                        atomicAdd(&sm.A[1][n], acca[o].y);
-                        atomicAdd(&sm.A[2][n], accb[o].x);
-                        atomicAdd(&sm.A[3][n], accb[o].y);
-                    }
+        for (int o = 0; o < 27; ++o) {
+            const float2 send = half ? acca[o] : accb[o];
+            float2 recv;
+            recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+            recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+            if (half) accb[o] = fadd2(accb[o], recv);
+            else acca[o] = fadd2(acca[o], recv);
         }
+        // add the cell stencils to the block window in 27 offset rounds: within
+        // a round every cell writes a different node, so no atomics are needed
+        // (shared-memory float atomics are a compare-and-swap loop on this GPU)
+        const int ch = half * 2;
+        const bool any = ncl > 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int o = (i * 3 + j) * 3 + k;
+                    __syncthreads();
+                    if (any) {
+                        const int n = (clz + 1 + k) * GAZ + (cly + 1 + j) * GA + (clx + 1 + i);
+                        const float2 val = half ? accb[o] : make_float2(acca[o].x * mp, acca[o].y);
+                        sm.A[ch][n] += val.x;
+                        sm.A[ch + 1][n] += val.y;
+                    }
+                }
     }
     __syncthreads();
     // 3. block window -> grid: one vector atomic per touched node
@@ -682,29 +686,19 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
         }
     }
     if (cands) {
+        // nearest particle to the next tip: CTA minimum, then one atomic per CTA that improves it
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long ok = __shfl_down_sync(0xffffffffu, best, o);
-            const float o0 = __shfl_down_sync(0xffffffffu, bpos[0], o);
-            const float o1 = __shfl_down_sync(0xffffffffu, bpos[1], o);
-            const float o2 = __shfl_down_sync(0xffffffffu, bpos[2], o);
-            if (ok < best) { best = ok; bpos[0] = o0; bpos[1] = o1; bpos[2] = o2; }
+            if (ok < best) best = ok;
         }
-        if (lane == 0) {
-            sm.key[tid >> 5] = best;
-            sm.pos[tid >> 5][0] = bpos[0];
-            sm.pos[tid >> 5][1] = bpos[1];
-            sm.pos[tid >> 5][2] = bpos[2];
-        }
+        if (lane == 0) sm.key[tid >> 5] = best;
         __syncthreads();
         if (tid == 0) {
-            int wbest = 0;
+            unsigned long long m = sm.key[0];
             for (int a = 1; a < NT / 32; ++a)
-                if (sm.key[a] < sm.key[wbest]) wbest = a;
-            Cand c;
-            c.key = sm.key[wbest];
-            c.x = sm.pos[wbest][0]; c.y = sm.pos[wbest][1]; c.z = sm.pos[wbest][2]; c.pad = 0.f;
-            d.cand[b] = c;
+                if (sm.key[a] < m) m = sm.key[a];
+            if (m < *((volatile unsigned long long *)&S->e_key)) atomicMin(&S->e_key, m);
         }
     }
 }
@@ -862,7 +856,7 @@ __global__ void k_surface_normal(const float *h, float *nrm, int W, int H, float
 
 static inline unsigned int cdiv(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
 
-void launch_round_begin(const Dev &d, cudaStream_t s) { k_round_begin<<<d.n_inst, 256, 0, s>>>(d); }
+void launch_round_begin(const Dev &d, cudaStream_t s) { k_round_begin<<<(d.n_inst + 127) / 128, 128, 0, s>>>(d); }
 void launch_set_end(const Dev &d, long long n, cudaStream_t s) { k_set_end<<<1, 1, 0, s>>>(d, n); }
 
 void launch_grid(const Dev &d, long long max_nodes, cudaStream_t s)
