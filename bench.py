@@ -92,10 +92,14 @@ class ClockSampler:
 
 
 def _kernel_hash():
-    h = hashlib.sha256()
-    for f in ("tsim_kernels.cu", "tsim_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2405_02914_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    """Hash of the fused transfer kernel's source (its section of
+    tsim_kernels.cu plus the device header it includes)."""
+    csrc = os.path.join(ROOT, "paper_2405_02914_gb300", "csrc")
+    k = open(os.path.join(csrc, "tsim_kernels.cu")).read()
+    a, b = k.index("// ---------------------------------------------------------------- fused transfer"), \
+        k.index("size_t transfer_smem_bytes()")
+    h = hashlib.sha256(k[a:b].encode())
+    h.update(open(os.path.join(csrc, "tsim_device.cuh"), "rb").read())
     return h.hexdigest()[:16]
 
 
