@@ -133,8 +133,8 @@ def cpu_baseline(scene, max_seconds=15.0):
         if el > max_seconds or done >= 50:
             break
     return {"value": x.shape[0] * passes / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "first %d substeps (%d passes) of the 4,194,304-particle pad press, FP64 oracle, "
-                      "serial, %.1f s" % (done, passes, el)}
+            "sample": "first %d substeps (%d passes) of a %d-particle scene of this workload, FP64 oracle, "
+                      "serial, %.1f s" % (done, passes, x.shape[0], el)}
 
 
 def run_reference(args, scene):
@@ -171,6 +171,22 @@ def run_reference(args, scene):
     print(json.dumps(line), flush=True)
 
 
+def workload(name, seed):
+    """Scenes of a named workload and its description."""
+    from paper_2405_02914_gb300 import inputs as I
+    if name == "pad4m":
+        return [I.scene_pad4m(seed=seed)], ("pad4m: 128x128x32 cells, dx=0.3125 mm, 4,194,304 particles, "
+                                            "press-slip-rotate")
+    if name == "press65k":
+        return [I.scene_press65k()], "press65k: 32x32x8 cells, dx=0.625 mm, 65,536 particles, sphere press"
+    if name == "large33m":
+        return [I.scene_large33m()], ("large33m: 256x256x64 cells, dx=0.234375 mm, 33,554,432 particles, "
+                                      "Perlin plate press-slip-rotate")
+    sc = I.batch_scenes(n=64, seed=seed)
+    n = sum(s.gel.n_particles for s in sc)
+    return sc, "batch64: 64 instances, grids 48x48x12..128x128x32, %d particles, lockstep" % n
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -179,13 +195,15 @@ def main():
     ap.add_argument("--impl", default="tsim", choices=["tsim", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="pad4m", choices=["pad4m", "press65k", "batch64", "large33m"])
     ap.add_argument("--no-graph", action="store_true",
                     help="launch kernels one by one (profilers cannot see inside graphs with loops)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     from paper_2405_02914_gb300 import inputs as I
-    scene = I.scene_pad4m(seed=args.seed)
+    scenes, wl_desc = workload(args.workload, args.seed)
+    scene = scenes[0]
     if args.impl == "reference":
         return run_reference(args, scene)
 
@@ -204,27 +222,38 @@ def main():
     stream = torch.cuda.current_stream()
 
     # inputs resident in HBM before the timed region
-    x, tag = I.gel_particles(scene.gel)
-    v, C, F = I.rest_state(x.shape[0])
-    n = x.shape[0]
-    d_in = [torch.from_numpy(a).to(dev) for a in (x, v, C, F)] + [torch.from_numpy(tag.view(np.int32)).to(dev)]
-    ctx = T.tsim_create([T.gel_desc(scene.gel)], [T.material_desc(scene.mat)], stream)
+    d_in = []
+    for sc in scenes:
+        x, tag = I.gel_particles(sc.gel)
+        v, C, F = I.rest_state(x.shape[0])
+        d_in.append([torch.from_numpy(a).to(dev) for a in (x, v, C, F)] +
+                    [torch.from_numpy(tag.view(np.int32)).to(dev)])
+        del x, tag, v, C, F
+    n = sum(sc.gel.n_particles for sc in scenes)
+    ctx = T.tsim_create([T.gel_desc(sc.gel) for sc in scenes], [T.material_desc(sc.mat) for sc in scenes],
+                        stream)
     T.tsim_set_solver(ctx, T.solver_desc(scene.solver))
-    T.tsim_set_indenter(ctx, 0, T.indenter_desc(scene.ind))
-    T.tsim_set_trajectory(ctx, 0, scene.keyframes)
+    for i, sc in enumerate(scenes):
+        T.tsim_set_indenter(ctx, i, T.indenter_desc(sc.ind))
+        T.tsim_set_trajectory(ctx, i, sc.keyframes)
     T.tsim_use_graph(ctx, not args.no_graph)
     T.tsim_profile(ctx, True)
-    W = H = scene.readout_px
-    h_out = torch.empty((H, W), device=dev)
-    n_out = torch.empty((H, W, 3), device=dev)
+    outs = [(torch.empty((sc.readout_px, sc.readout_px), device=dev),
+             torch.empty((sc.readout_px, sc.readout_px, 3), device=dev)) for sc in scenes]
 
     def reset():
         T.tsim_set_substep(ctx, 0)
-        T.tsim_write_particles(ctx, 0, *d_in)
+        for i in range(len(scenes)):
+            T.tsim_write_particles(ctx, i, *d_in[i])
+
+    def read_all(host=False):
+        for i, sc in enumerate(scenes):
+            h, nrm = (h_hosts[i], n_hosts[i]) if host else outs[i]
+            T.tsim_read_surface(ctx, i, sc.readout_px, sc.readout_px, sc.readout_pitch, h, nrm)
 
     def one_step():
         T.tsim_step(ctx, SUBSTEPS_PER_STEP)
-        T.tsim_read_surface(ctx, 0, W, H, scene.readout_pitch, h_out, n_out)
+        read_all()
 
     reset()
     for _ in range(args.warmup):
@@ -255,23 +284,25 @@ def main():
     substeps = s1.substeps - s0.substeps
 
     # end to end through the public API with host buffers (pinned)
-    kf_host = T.keyframes(scene.keyframes)
-    h_host = torch.empty((H, W), pin_memory=True)
-    n_host = torch.empty((H, W, 3), pin_memory=True)
+    kf_hosts = [T.keyframes(sc.keyframes) for sc in scenes]
+    h_hosts = [torch.empty((sc.readout_px, sc.readout_px), pin_memory=True) for sc in scenes]
+    n_hosts = [torch.empty((sc.readout_px, sc.readout_px, 3), pin_memory=True) for sc in scenes]
+
+    def e2e_step():
+        for i in range(len(scenes)):
+            T.tsim_set_trajectory(ctx, i, kf_hosts[i])
+        T.tsim_step(ctx, SUBSTEPS_PER_STEP)
+        read_all(host=True)
+
     reset()
     T.tsim_profile(ctx, False)
-    for _ in range(1):
-        T.tsim_set_trajectory(ctx, 0, kf_host)
-        T.tsim_step(ctx, SUBSTEPS_PER_STEP)
-        T.tsim_read_surface(ctx, 0, W, H, scene.readout_pitch, h_host, n_host)
+    e2e_step()
     reset()
     s2 = T.tsim_stats(ctx)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        T.tsim_set_trajectory(ctx, 0, kf_host)
-        T.tsim_step(ctx, SUBSTEPS_PER_STEP)
-        T.tsim_read_surface(ctx, 0, W, H, scene.readout_pitch, h_host, n_host)
+        e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     s3 = T.tsim_stats(ctx)
@@ -300,29 +331,32 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "pad4m: 128x128x32 cells, dx=0.3125 mm, 4,194,304 particles, "
-                               "press-slip-rotate, %d substeps + 128x128 surface readout per step"
-                               % SUBSTEPS_PER_STEP,
+        "config": {"workload": "%s, %d substeps + surface readout per step" % (wl_desc, SUBSTEPS_PER_STEP),
+                   "instances": len(scenes),
                    "particles": n, "substeps_timed": int(substeps), "passes_timed": int(passes),
-                   "mean_passes_per_substep": passes / max(substeps, 1),
+                   "mean_passes_per_substep": passes / max(substeps * len(scenes), 1),
                    "particle_substeps_per_s": n * substeps * world / (t_max * 1e-3),
+                   "substep_ms": t_max / max(substeps, 1),
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (particle state 436 MB per parity)",
+                   "l2": "inputs larger than L2 (particle state %d MB per parity)" % (n * 52 // 2 ** 20),
                    "surrogate_frames_per_s": None},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _traffic(n),
                      "kernel": "k_transfer<COMMIT> (fused G2P -> F,x move -> re-bin -> P2G)",
                      "launches_timed": launches, "avg_launch_ms": avg_commit_ms,
                      "bytes_per_launch": n * BYTES_PER_UPDATE, "peak_source": peak_kind},
-        "e2e": {"value": e2e_tot / e2e_max, "unit": UNIT, "h2d_bytes_per_step": 20 * len(kf_host),
-                "d2h_bytes_per_step": 4 * W * H * 4},
+        "e2e": {"value": e2e_tot / e2e_max, "unit": UNIT,
+                "h2d_bytes_per_step": sum(20 * len(k) for k in kf_hosts),
+                "d2h_bytes_per_step": sum(16 * sc.readout_px ** 2 for sc in scenes)},
         "gpu_launches": None,
         "clocks": clk,
     }
     # own kernels launched in the timed region: per substep round_begin, grid, check,
     # commit transfer; per extra pass transfer, grid, check; per step 3 readout kernels
     extra = passes - substeps
-    line["gpu_launches"] = int(4 * substeps + 3 * extra + 3 * args.steps) * world
+    line["gpu_launches"] = int(4 * substeps + 3 * extra + 3 * args.steps * len(scenes)) * world
+    if args.workload != "pad4m":
+        line["metric"] = UNIT + " (%s)" % args.workload
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene)
     print(json.dumps(line), flush=True)

@@ -380,7 +380,9 @@ def batch_scenes(n: int = 64, seed: int = 0, scale: float = 1.0) -> List[Scene]:
         n_slip = int(math.ceil(slip / (0.2 * dt))) if slip > 0 else 0
         n_rot = int(math.ceil(rot / (40.0 * dt))) if rot > 0 else 0
         L = gel.cx * gel.dx
-        kf = press_slip_rotate((L / 2 - slip / 2, L / 2, gel.height), press, slip, rot,
+        # the tip starts 0.37 dx above the gel so that no flat face sits on a node plane
+        gap = 0.37 * gel.dx
+        kf = press_slip_rotate((L / 2 - slip / 2, L / 2, gel.height + gap), press + gap, slip, rot,
                                n_press, n_slip, n_rot)
         scenes.append(Scene(gel, mat, ind, kf, Solver(dt=dt), readout_every=100,
                             readout_px=gel.cx, readout_pitch=gel.dx,

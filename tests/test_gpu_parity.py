@@ -304,3 +304,69 @@ def test_pad4m_full_size_sampled_one_step():
         O.substep(s, ind, sc.keyframes, 600, st)
         assert np.abs(x1[m][core] - st.x[core]).max() < 1e-4 * dx
         assert np.abs(F1[m][core] - st.F[core]).max() < 1e-5
+
+
+# ------------------------------------------------------------------ batching
+
+def test_seeded_uneven_batch_matches_oracle():
+    """Eight seeded instances of the batched workload's generator (grids
+    16-32 cells, E, nu, mu and indenters drawn per instance), one context,
+    300 substeps in the graph launch configuration, each against the oracle."""
+    scenes = I.batch_scenes(n=8, seed=3, scale=0.25)
+    states = [_init(sc) for sc in scenes]
+    sim = T.Sim(scenes, use_graph=True, states=states)
+    sim.step(300)
+    for i, sc in enumerate(scenes):
+        st, s, ind = _oracle(sc, states[i])
+        pl, _ = O.run(s, ind, sc.keyframes, 0, 300, st)
+        x, _, _, _ = T.tsim_read_particles(sim.ctx, i, sc.gel.n_particles)
+        gp, _ = T.tsim_read_log(sim.ctx, i, 300)
+        assert float(np.mean(gp == pl)) > 0.98, i
+        assert np.abs(x - st.x).max() < POS_TOL * sc.gel.dx, i
+    sim.close()
+
+
+def test_instances_do_not_interact():
+    """An instance advanced inside a batch equals the same instance alone
+    (up to the order of floating-point atomics)."""
+    scenes = I.batch_scenes(n=3, seed=5, scale=0.2)
+    states = [_init(sc) for sc in scenes]
+    batch = T.Sim(scenes, use_graph=True, states=states)
+    batch.step(120)
+    for i, sc in enumerate(scenes):
+        alone = T.Sim([sc], use_graph=True, states=[states[i]])
+        alone.step(120)
+        xa, _, _, _ = alone.particles()
+        xb, _, _, _ = T.tsim_read_particles(batch.ctx, i, sc.gel.n_particles)
+        alone.close()
+        assert np.abs(xa - xb).max() < 1e-5 * sc.gel.dx, i
+    batch.close()
+
+
+def test_large33m_prefix_sampled_one_step():
+    """33,554,432-particle gel with the Perlin-bump plate: after a 500-substep
+    prefix on the GPU, one substep of sampled sub-boxes matches the oracle on
+    the same snapshot, P2G conserves mass and the 16x16 markers read back
+    the particles' positions."""
+    sc = I.scene_large33m()
+    sim = T.Sim(sc, use_graph=True)
+    sim.step(500)
+    x, v, C, F = sim.particles()
+    tag = I.gel_particles(sc.gel)[1]
+    g = sim.grid()
+    mp = sc.mat.rho * sc.gel.dx ** 3 / 8
+    assert abs(g[:, 0].astype(np.float64).sum() / (x.shape[0] * mp) - 1) < 1e-4
+    ids = I.marker_ids(sc.gel, 16)
+    mk = T.tsim_read_markers(sim.ctx, 0, ids)
+    assert np.array_equal(mk, x[ids])
+    sim.step(1)
+    x1, _, _, F1 = sim.particles()
+    sim.close()
+    dx = sc.gel.dx
+    s, ind = O.make_scene(sc), O.make_indenter(sc.ind)
+    for lo, hi in [((120, 120, 56), (134, 134, 63)), ((0, 0, -1), (8, 8, 6)), ((200, 40, 30), (212, 52, 40))]:
+        m, core = _subset((x,), lo, hi, dx)
+        st = O.State(x[m], v[m], C[m], F[m], tag[m])
+        O.substep(s, ind, sc.keyframes, 500, st)
+        assert np.abs(x1[m][core] - st.x[core]).max() < 1e-4 * dx
+        assert np.abs(F1[m][core] - st.F[core]).max() < 1e-5
