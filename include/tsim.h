@@ -197,6 +197,25 @@ int tsim_read_grid(tsim_ctx *ctx, int inst, float *out, int on_device);
 int tsim_read_surface(tsim_ctx *ctx, int inst, float *height, float *normal, int W, int H,
                       float pitch, int on_device);
 
+/* Displacement field of instance inst: u[H*W*3] = the 2-D quadratic
+ * B-spline average over TSIM_TAG_TOP particles of x - X, with the weights
+ * taken at each particle's reference position X (x_ref[n*3], particle-id
+ * order, host or device per on_device) on the pixel grid of
+ * tsim_read_surface; pixels with no particle read 0.  W*H <= 1<<19.  This
+ * is the surface displacement that the learned surrogate is trained on
+ * (Sec. IV-B depth map, taken per component).  Synchronises. */
+int tsim_read_displacement(tsim_ctx *ctx, int inst, const float *x_ref, float *u, int W, int H, float pitch,
+                           int on_device);
+
+/* Height of the indenter's underside above the gel top, h[H*W], at the pose
+ * of the next substep, on the pixel grid of tsim_read_surface: the first
+ * crossing of the SDF zero level going up each pixel column from
+ * gel top - clip (sphere tracing, at most 128 steps); columns that miss the
+ * shape read +clip; values are clamped to [-clip, clip].  This is the
+ * indenter heightmap that the surrogate takes as input.  Synchronises. */
+int tsim_read_indenter_height(tsim_ctx *ctx, int inst, float *h, int W, int H, float pitch, float clip,
+                              int on_device);
+
 /* Positions of m particles given by id (ids[m], host) of instance inst:
  * xyz[m*3].  Used for embedded marker tracks.  Synchronises. */
 int tsim_read_markers(tsim_ctx *ctx, int inst, const int32_t *ids, int m, float *xyz,

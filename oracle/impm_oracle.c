@@ -605,3 +605,66 @@ void orc_surface(int n, const double *x, const uint32_t *tag, int W, int H, doub
         }
     free(num); free(den);
 }
+
+/* ------------------------------------------------------------------ surrogate inputs/targets */
+
+/* Displacement x - X of the top-layer particles, splatted with the 2-D
+ * quadratic B-spline at the reference positions X; empty pixels read 0. */
+void orc_surface_disp(int n, const double *x, const double *xref, const uint32_t *tag, int W, int H,
+                      double pitch, double *u)
+{
+    double *acc = (double *)calloc((size_t)W * H * 4, sizeof(double));
+    for (int p = 0; p < n; ++p) {
+        if (!(tag[p] & ORC_TAG_TOP)) continue;
+        double px = xref[p * 3] / pitch - 0.5, py = xref[p * 3 + 1] / pitch - 0.5;
+        int u0 = (int)floor(px) - 1, v0 = (int)floor(py) - 1;
+        for (int b = v0; b <= v0 + 3; ++b)
+            for (int a = u0; a <= u0 + 3; ++a) {
+                if (a < 0 || b < 0 || a >= W || b >= H) continue;
+                double w = bspline2(px - a) * bspline2(py - b);
+                if (w == 0.0) continue;
+                double *c = acc + ((long)b * W + a) * 4;
+                for (int d = 0; d < 3; ++d) c[d] += w * (x[p * 3 + d] - xref[p * 3 + d]);
+                c[3] += w;
+            }
+    }
+    for (long i = 0; i < (long)W * H; ++i)
+        for (int d = 0; d < 3; ++d) u[i * 3 + d] = acc[i * 4 + 3] > 0.0 ? acc[i * 4 + d] / acc[i * 4 + 3] : 0.0;
+    free(acc);
+}
+
+/* Height of the indenter's underside above the gel top H per pixel column:
+ * scan up from H - clip in steps of `step` and bisect the first entry into
+ * the shape (phi <= 0) to 1e-13 m; a column that starts inside reads -clip,
+ * one that never enters the shape below H + clip reads +clip. */
+void orc_indenter_height(const orc_indenter *ind, const orc_pose *ps, double Hgel, int W, int H, double pitch,
+                         double clip, double step, double *h)
+{
+    for (int v = 0; v < H; ++v)
+        for (int a = 0; a < W; ++a) {
+            double xw[3] = {(a + 0.5) * pitch, (v + 0.5) * pitch, Hgel - clip}, nrm[3];
+            double out = clip;
+            double lo = xw[2];
+            if (orc_sdf(ind, ps, xw, nrm) <= 0.0) {
+                out = -clip;
+            } else {
+                for (double z = lo + step; z <= Hgel + clip + step; z += step) {
+                    xw[2] = z;
+                    if (orc_sdf(ind, ps, xw, nrm) <= 0.0) {
+                        double hi = z;                 /* phi(lo) > 0 >= phi(hi) */
+                        while (hi - lo > 1e-13) {
+                            double mid = 0.5 * (lo + hi);
+                            xw[2] = mid;
+                            if (orc_sdf(ind, ps, xw, nrm) <= 0.0) hi = mid; else lo = mid;
+                        }
+                        out = 0.5 * (lo + hi) - Hgel;
+                        break;
+                    }
+                    lo = z;
+                }
+            }
+            if (out > clip) out = clip;
+            if (out < -clip) out = -clip;
+            h[(long)v * W + a] = out;
+        }
+}

@@ -92,6 +92,9 @@ def lib():
             L.orc_run.restype = C.c_int
             L.orc_surface.argtypes = [C.c_int, _D, _U, C.c_int, C.c_int, C.c_double, C.c_double,
                                       _D, _D]
+            L.orc_surface_disp.argtypes = [C.c_int, _D, _D, _U, C.c_int, C.c_int, C.c_double, _D]
+            L.orc_indenter_height.argtypes = [P(Indenter), P(Pose), C.c_double, C.c_int, C.c_int, C.c_double,
+                                              C.c_double, C.c_double, _D]
             _lib = L
     return _lib
 
@@ -269,3 +272,19 @@ def surface(st: State, W: int, H: int, pitch: float, h_empty: float):
 
 def lame(E: float, nu: float):
     return E / (2 * (1 + nu)), E * nu / ((1 + nu) * (1 - 2 * nu))
+
+
+def surface_disp(st: State, xref, W: int, H: int, pitch: float):
+    """Displacement of the top layer splatted at the reference positions."""
+    u = np.zeros(W * H * 3)
+    xref = np.ascontiguousarray(xref, dtype=np.float64).reshape(-1, 3)
+    lib().orc_surface_disp(st.n, st.x, xref, st.tag, W, H, float(pitch), u)
+    return u.reshape(H, W, 3)
+
+
+def indenter_height(ind: Indenter, ps: Pose, gel_height: float, W: int, H: int, pitch: float, clip: float,
+                    step: float):
+    h = np.zeros(W * H)
+    lib().orc_indenter_height(C.byref(ind), C.byref(ps), float(gel_height), W, H, float(pitch), float(clip),
+                              float(step), h)
+    return h.reshape(H, W)

@@ -742,6 +742,44 @@ extern "C" int tsim_read_surface(tsim_ctx *c, int inst, float *height, float *no
     return latched(c);
 }
 
+extern "C" int tsim_read_displacement(tsim_ctx *c, int inst, const float *x_ref, float *u, int W, int H,
+                                      float pitch, int on_device)
+{
+    int rc = check_ctx(c, inst);
+    if (rc) return rc;
+    if (!x_ref || !u || W < 1 || H < 1 || (long long)W * H > RO_MAX / 2 || !(pitch > 0.f))
+        return fail(TSIM_ERR_INVALID_ARG, "need x_ref, u, 1 <= W*H <= 2^19 and pitch > 0");
+    if (!c->have_particles[inst]) return fail(TSIM_ERR_STATE, "no particles written");
+    const Inst &I = c->hinst[inst];
+    const size_t WH = (size_t)W * H;
+    const float *xr = x_ref;
+    if (!on_device) {       // reference positions go through the id-ordered staging velocity buffer
+        CU(cudaMemcpyAsync(c->d.sv + (size_t)I.id0 * 3, x_ref, sizeof(float) * 3 * (size_t)I.n_particles,
+                           cudaMemcpyHostToDevice, c->stream));
+        xr = c->d.sv + (size_t)I.id0 * 3;
+    }
+    float *acc = c->ro, *uf = c->ro + 4 * WH;
+    launch_surface_disp(c->d, inst, I.nblocks, c->par_next, xr, acc, uf, W, H, pitch, c->stream);
+    CU(cudaGetLastError());
+    rc = copy_out(c, u, uf, sizeof(float) * 3 * WH, on_device);
+    if (rc) return rc;
+    return latched(c);
+}
+
+extern "C" int tsim_read_indenter_height(tsim_ctx *c, int inst, float *h, int W, int H, float pitch, float clip,
+                                         int on_device)
+{
+    int rc = check_ctx(c, inst);
+    if (rc) return rc;
+    if (!h || W < 1 || H < 1 || (long long)W * H > RO_MAX || !(pitch > 0.f) || !(clip > 0.f))
+        return fail(TSIM_ERR_INVALID_ARG, "need h, 1 <= W*H <= 2^20, pitch > 0, clip > 0");
+    launch_indenter_height(c->d, inst, c->ro, W, H, pitch, clip, c->stream);
+    CU(cudaGetLastError());
+    rc = copy_out(c, h, c->ro, sizeof(float) * (size_t)W * H, on_device);
+    if (rc) return rc;
+    return latched(c);
+}
+
 extern "C" int tsim_read_markers(tsim_ctx *c, int inst, const int32_t *ids, int m, float *xyz, int on_device)
 {
     int rc = check_ctx(c, inst);

@@ -852,6 +852,82 @@ __global__ void k_surface_normal(const float *h, float *nrm, int W, int H, float
     nrm[t * 3 + 2] = L;
 }
 
+// Displacement u = x - X of the surface particles, splatted with the 2-D
+// quadratic B-spline at their reference positions X (Lagrangian field).
+__global__ void k_surface_disp(Dev d, int inst, int par, const float *__restrict__ xref, float *acc, int W,
+                               int H, float inv_pitch)
+{
+    const Inst &I = d.inst[inst];
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)I.nblocks * CAP) return;
+    const int b = I.block0 + (int)(t / CAP), r = (int)(t % CAP);
+    if (r >= min(d.cnt[par][b], CAP)) return;
+    const long long SS = d.S, slot = (long long)b * CAP + r;
+    const uint32_t tag = d.T[par][slot];
+    if (!(tag & TAG_TOP)) return;
+    const uint32_t id = tag & ID_MASK;
+    if (id >= (uint32_t)I.n_particles) return;
+    const float *P = d.P[par];
+    const float X = xref[(long long)id * 3], Y = xref[(long long)id * 3 + 1], Z = xref[(long long)id * 3 + 2];
+    const float ux = P[slot] - X, uy = P[SS + slot] - Y, uz = P[2 * SS + slot] - Z;
+    const float px = X * inv_pitch - 0.5f, py = Y * inv_pitch - 0.5f;
+    const int u0 = (int)floorf(px) - 1, v0 = (int)floorf(py) - 1;
+    for (int bb = v0; bb <= v0 + 3; ++bb) {
+        if (bb < 0 || bb >= H) continue;
+        const float wy = bspline_kernel(py - (float)bb);
+        if (wy == 0.f) continue;
+        for (int a = u0; a <= u0 + 3; ++a) {
+            if (a < 0 || a >= W) continue;
+            const float w = bspline_kernel(px - (float)a) * wy;
+            if (w == 0.f) continue;
+            float *c = acc + ((long long)bb * W + a) * 4;
+            atomicAdd(c, w * ux);
+            atomicAdd(c + 1, w * uy);
+            atomicAdd(c + 2, w * uz);
+            atomicAdd(c + 3, w);
+        }
+    }
+}
+
+__global__ void k_surface_disp_finish(const float *acc, float *u, int WH)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= WH) return;
+    const float w = acc[t * 4 + 3];
+    const float iw = w > 0.f ? 1.f / w : 0.f;
+    u[t * 3] = acc[t * 4] * iw;
+    u[t * 3 + 1] = acc[t * 4 + 1] * iw;
+    u[t * 3 + 2] = acc[t * 4 + 2] * iw;
+}
+
+// Height of the indenter's underside above the gel top at the current pose
+// (the pose of the next substep), by sphere tracing the SDF straight up each
+// pixel column from gel top - clip; columns that miss the shape read +clip,
+// heights are clamped to [-clip, clip].
+__global__ void k_indenter_height(Dev d, int inst, float *h, int W, int H, float pitch, float clip)
+{
+    __shared__ Pose P;
+    const Inst &I = d.inst[inst];
+    if (threadIdx.x == 0) pose_eval(I, d.kf + (long long)inst * MAX_KF * 5, d.G->k_next, P);
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= W * H) return;
+    const float xw0 = ((t % W) + 0.5f) * pitch, xw1 = ((t / W) + 0.5f) * pitch;
+    if (I.ind_kind == K_NONE) { h[t] = clip; return; }
+    const int *perm = d.perm + inst * 256;
+    float z = I.H - clip;
+    float out = clip;
+    for (int it = 0; it < 128; ++it) {
+        const float xw[3] = {xw0, xw1, z};
+        float n[3];
+        const float phi = sdf_world(I, perm, P, xw, n);
+        if (phi < 1e-4f * I.dx) { out = z - I.H; break; }
+        z += 0.8f * phi;
+        if (z > I.H + clip) break;
+    }
+    h[t] = fminf(fmaxf(out, -clip), clip);
+}
+
 // ---------------------------------------------------------------- launchers
 
 static inline unsigned int cdiv(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
@@ -914,6 +990,19 @@ void launch_surface(const Dev &d, int inst, int nblocks, int par, float *num, fl
                                                                           1.f / pitch);
     k_surface_height<<<cdiv((long long)W * H, 256), 256, 0, s>>>(num, den, h, W * H, h_empty);
     k_surface_normal<<<cdiv((long long)W * H, 256), 256, 0, s>>>(h, nrm, W, H, pitch);
+}
+
+void launch_surface_disp(const Dev &d, int inst, int nblocks, int par, const float *xref, float *acc, float *u,
+                         int W, int H, float pitch, cudaStream_t s)
+{
+    cudaMemsetAsync(acc, 0, sizeof(float) * 4 * (size_t)W * H, s);
+    k_surface_disp<<<cdiv((long long)nblocks * CAP, 256), 256, 0, s>>>(d, inst, par, xref, acc, W, H, 1.f / pitch);
+    k_surface_disp_finish<<<cdiv((long long)W * H, 256), 256, 0, s>>>(acc, u, W * H);
+}
+
+void launch_indenter_height(const Dev &d, int inst, float *h, int W, int H, float pitch, float clip, cudaStream_t s)
+{
+    k_indenter_height<<<cdiv((long long)W * H, 128), 128, 0, s>>>(d, inst, h, W, H, pitch, clip);
 }
 
 // kernel handles for graph construction

@@ -19,6 +19,9 @@ void launch_pick(const Dev &d, int inst, const int *ids, int m, float *out, cuda
 void launch_surface(const Dev &d, int inst, int nblocks, int par, float *num, float *den, float *h,
                     float *nrm, int W, int H, float pitch, float h_empty, cudaStream_t s);
 
+void launch_surface_disp(const Dev &d, int inst, int nblocks, int par, const float *xref, float *acc, float *u,
+                         int W, int H, float pitch, cudaStream_t s);
+void launch_indenter_height(const Dev &d, int inst, float *h, int W, int H, float pitch, float clip, cudaStream_t s);
 cudaError_t setup_kernels();
 size_t transfer_smem_bytes();
 

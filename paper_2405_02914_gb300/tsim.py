@@ -24,7 +24,7 @@ EXPORTS = ["tsim_create", "tsim_set_solver", "tsim_set_indenter", "tsim_set_traj
            "tsim_write_particles", "tsim_set_substep", "tsim_step", "tsim_read_particles",
            "tsim_read_grid", "tsim_read_surface", "tsim_read_markers", "tsim_read_log", "tsim_sync",
            "tsim_stats", "tsim_use_graph", "tsim_profile", "tsim_kernel_time", "tsim_last_error",
-           "tsim_destroy", "tsim_p2g_noalloc"]
+           "tsim_destroy", "tsim_p2g_noalloc", "tsim_read_displacement", "tsim_read_indenter_height"]
 
 
 class TsimError(RuntimeError):
@@ -84,6 +84,9 @@ def load():
             "tsim_read_grid": (C.c_int, [vp, C.c_int, vp, C.c_int]),
             "tsim_read_surface": (C.c_int, [vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_float, C.c_int]),
             "tsim_read_markers": (C.c_int, [vp, C.c_int, vp, C.c_int, vp, C.c_int]),
+            "tsim_read_displacement": (C.c_int, [vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_float, C.c_int]),
+            "tsim_read_indenter_height": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, C.c_float, C.c_float,
+                                                    C.c_int]),
             "tsim_read_log": (C.c_int, [vp, C.c_int, vp, vp, C.c_int]),
             "tsim_sync": (C.c_int, [vp]),
             "tsim_stats": (C.c_int, [vp, P(Stats)]),
@@ -259,6 +262,23 @@ def tsim_read_surface(ctx, inst, W, H, pitch, height=None, normal=None):
     pn, _, _ = _ptr(n, np.float32)
     _check(load().tsim_read_surface(ctx, inst, ph, pn, int(W), int(H), float(pitch), on))
     return h, n
+
+
+def tsim_read_displacement(ctx, inst, x_ref, W, H, pitch, out=None):
+    arr = np.empty((H, W, 3), np.float32) if out is None else out
+    pr, onr, keep = _ptr(x_ref, np.float32)
+    p, on, _ = _ptr(arr, np.float32)
+    if onr != on:
+        raise ValueError("x_ref and out must both be host or both be device arrays")
+    _check(load().tsim_read_displacement(ctx, inst, pr, p, int(W), int(H), float(pitch), on))
+    return arr
+
+
+def tsim_read_indenter_height(ctx, inst, W, H, pitch, clip, out=None):
+    arr = np.empty((H, W), np.float32) if out is None else out
+    p, on, _ = _ptr(arr, np.float32)
+    _check(load().tsim_read_indenter_height(ctx, inst, p, int(W), int(H), float(pitch), float(clip), on))
+    return arr
 
 
 def tsim_read_markers(ctx, inst, ids, out=None):

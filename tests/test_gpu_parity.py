@@ -370,3 +370,34 @@ def test_large33m_prefix_sampled_one_step():
         O.substep(s, ind, sc.keyframes, 500, st)
         assert np.abs(x1[m][core] - st.x[core]).max() < 1e-4 * dx
         assert np.abs(F1[m][core] - st.F[core]).max() < 1e-5
+
+
+# ------------------------------------------------------------------ surrogate inputs and targets
+
+@pytest.mark.parametrize("kind", [I.SPHERE, I.CYLINDER, I.PRISM, I.PERLIN])
+def test_displacement_and_indenter_height_match_oracle(kind):
+    """The displacement field (splat of x - X at the reference positions) and
+    the indenter underside height map against the oracle; the heights are
+    found by sphere tracing on the GPU and by scan + bisection in the oracle."""
+    sc = I.scene_small(cx=16, cy=16, cz=4, kind=kind, n_press=120, press=0.2e-3, slip=0.1e-3, n_slip=30)
+    x0, tag = I.gel_particles(sc.gel)
+    sim = T.Sim(sc)
+    sim.step(150)
+    x, v, C, F = sim.particles()
+    W, pitch, clip = 32, sc.gel.dx / 2, 2e-3
+    u = T.tsim_read_displacement(sim.ctx, 0, x0, W, W, pitch)
+    h = T.tsim_read_indenter_height(sim.ctx, 0, W, W, pitch, clip)
+    sim.close()
+    uo = O.surface_disp(O.State(x, v, C, F, tag), x0, W, W, pitch)
+    assert np.abs(u - uo).max() < 1e-4 * np.abs(uo).max() + 1e-10
+    assert np.abs(uo[..., 2]).max() > 1e-5                        # the surface was pressed
+    ind = O.make_indenter(sc.ind)
+    ps = O.pose(sc.keyframes, 150, sc.solver.dt, sc.ind.tip_offset)
+    ho = O.indenter_height(ind, ps, sc.gel.height, W, W, pitch, clip, 1e-6)
+    hit = ho < clip
+    assert hit.sum() > 4
+    # sphere tracing from below stops within 1e-4 dx of the surface and never passes it
+    assert np.all(h[hit] <= ho[hit] + 1e-6 * sc.gel.dx)
+    assert np.median(np.abs(h[hit] - ho[hit])) < 1e-3 * sc.gel.dx
+    assert np.abs(h[hit] - ho[hit]).max() < 0.05 * sc.gel.dx
+    assert np.all(h[~hit] == np.float32(clip))
