@@ -388,3 +388,49 @@ def batch_scenes(n: int = 64, seed: int = 0, scale: float = 1.0) -> List[Scene]:
                             readout_px=gel.cx, readout_pitch=gel.dx,
                             n_substeps=n_press + n_slip + n_rot, name="batch"))
     return scenes
+
+
+# ------------------------------------------------------------------ surface surrogate inputs
+
+# (cin, cout) of the surrogate's nine 3x3 convolutions in parameter order; the
+# first layer's 16 inputs hold 12 real channels, the last layer's 16 rows 4 real ones
+SURR_CONVS = [(16, 32), (32, 64), (64, 128), (128, 256), (256, 256), (256, 128), (128, 64), (64, 32), (32, 16)]
+SURR_CIN, SURR_COUT = 12, 4
+
+
+def surrogate_params(seed: int, bias_std: float = 0.0, scale_last: float = 0.1) -> np.ndarray:
+    """Flat FP32 parameter vector, layer by layer W[cout][3][3][cin] then b[cout]:
+    He-normal weights on the real channels (the last layer scaled by
+    ``scale_last``), zero on the padded ones, biases N(0, bias_std)."""
+    rng = np.random.Generator(np.random.Philox(key=0x5A77 + seed))
+    parts = []
+    last = len(SURR_CONVS) - 1
+    for li, (cin, cout) in enumerate(SURR_CONVS):
+        rin = SURR_CIN if li == 0 else cin
+        rout = SURR_COUT if li == last else cout
+        w = np.zeros((cout, 3, 3, cin), np.float32)
+        std = math.sqrt(2.0 / (9 * rin)) * (scale_last if li == last else 1.0)
+        w[:rout, :, :, :rin] = rng.standard_normal((rout, 3, 3, rin)) * std
+        b = np.zeros(cout, np.float32)
+        if bias_std > 0:
+            b[:rout] = rng.standard_normal(rout) * bias_std
+        parts += [w.ravel(), b]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def surrogate_batch(seed: int, B: int, H: int, W: int, mask_frac: float = 0.8):
+    """Random features x[B,H,W,12] (one smooth bump channel, eleven per-sample
+    constants), targets t[B,H,W,3] and a 0/1 mask[B,H,W] covering a centred
+    window of about ``mask_frac`` of each side."""
+    rng = np.random.Generator(np.random.Philox(key=0x5B47 + seed))
+    x = np.empty((B, H, W, SURR_CIN), np.float32)
+    yy, xx = np.meshgrid(np.linspace(-1, 1, H), np.linspace(-1, 1, W), indexing="ij")
+    for b in range(B):
+        cy, cx, r = rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5), rng.uniform(0.2, 0.6)
+        x[b, :, :, 0] = np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2) / (r * r))
+        x[b, :, :, 1:] = rng.standard_normal(SURR_CIN - 1).astype(np.float32)
+    t = (rng.standard_normal((B, H, W, 3)) * 0.5).astype(np.float32)
+    m = np.zeros((B, H, W), np.float32)
+    my, mx = int(round(H * (1 - mask_frac) / 2)), int(round(W * (1 - mask_frac) / 2))
+    m[:, my:H - my, mx:W - mx] = 1.0
+    return x, t, m
