@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtsim.so")
-UNITS = ["tsim_kernels.cu", "tsim_api.cu", "tsim_noalloc.cu"]
+UNITS = ["tsim_kernels.cu", "tsim_api.cu", "tsim_noalloc.cu", "tsurr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-Xptxas", "-v"]
@@ -30,9 +30,9 @@ def _nvcc() -> str:
 
 
 def _deps():
-    inc = os.path.join(os.path.dirname(HERE), "include", "tsim.h")
+    inc = [os.path.join(os.path.dirname(HERE), "include", h) for h in ("tsim.h", "tsurr.h")]
     files = [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".cu", ".cuh", ".h"))]
-    return files + [inc]
+    return files + inc
 
 
 def up_to_date() -> bool:

@@ -1,0 +1,700 @@
+// tsurr.cu -- learned surface surrogate: convolutions as implicit GEMMs on the
+// BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate), forward, data
+// gradient and weight gradient; fused bias / skip / ReLU epilogues; nearest
+// upsampling fused into the input gather; masked loss with a residual
+// indicator channel; Adam.  Architecture and loss: include/tsurr.h.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tsim.h"
+#include "../../include/tsurr.h"
+
+void tsim_record_error(const std::string &msg);   // tsim_api.cu: the text tsim_last_error returns
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int BM = 64, BN = 64, BK = 16, GT = 128;   // CTA tile and threads (4 warps of 32x32)
+constexpr int NL = 9;
+constexpr int CIN_PAD = 16, COUT_PAD = 16;
+
+__device__ __forceinline__ float bf2f(bf16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ bf16 f2bf(float v) { return __float2bfloat16_rn(v); }
+
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// One BK = 16 step of the warp's 32x32 tile.  A is stored [m][k] and B [n][k]
+// in shared memory with a row stride of S 32-bit words (two BF16 each).
+template <int S>
+__device__ __forceinline__ void mma_tile(const uint32_t *A32, const uint32_t *B32, float acc[2][4][4], int wm,
+                                         int wn, int lane)
+{
+    const int gid = lane >> 2, tig = lane & 3;
+    uint32_t a[2][4], b[4][2];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi) {
+        const int r = wm * 32 + mi * 16 + gid;
+        a[mi][0] = A32[r * S + tig];
+        a[mi][1] = A32[(r + 8) * S + tig];
+        a[mi][2] = A32[r * S + 4 + tig];
+        a[mi][3] = A32[(r + 8) * S + 4 + tig];
+    }
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) {
+        const int n = wn * 32 + ni * 8 + gid;
+        b[ni][0] = B32[n * S + tig];
+        b[ni][1] = B32[n * S + 4 + tig];
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) mma16816(acc[mi][ni], a[mi], b[ni]);
+}
+
+struct Conv {
+    const bf16 *in;          // physical input [B][hin][win][cin]
+    int B, hin, win, cin;
+    int up, stride;          // logical input = nearest x2 of in when up; output = logical / stride
+    int hl, wl, hout, wout, cout;
+    const bf16 *w;           // [cout][3][3][cin]
+    const bf16 *wT;          // [cin][3][3][cout]
+    const float *bias;
+    const bf16 *skip;        // added before the ReLU (same shape as the output) or null
+    int relu;
+    bf16 *out;               // [B][hout][wout][cout] BF16, or
+    float *out32;            // FP32 output keeping the first out32_ch channels
+    int out32_ch;
+};
+
+// ---------------------------------------------------------------- forward
+
+__global__ void __launch_bounds__(GT) k_conv_fwd(Conv c)
+{
+    __shared__ __align__(16) bf16 As[BM][BK];
+    __shared__ __align__(16) bf16 Bs[BN][BK];
+    const int M = c.B * c.hout * c.wout, N = c.cout, K = 9 * c.cin;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, wm = warp & 1, wn = warp >> 1;
+    const int lr = t >> 1, lh = t & 1;
+    const int m = m0 + lr, n = n0 + lr;
+    const bool mv = m < M, nv = n < N;
+    int bb = 0, oy = 0, ox = 0;
+    if (mv) { ox = m % c.wout; oy = (m / c.wout) % c.hout; bb = m / (c.wout * c.hout); }
+    auto load = [&](int kt, uint4 &va, uint4 &vb) {
+        const int kk = kt / c.cin, ci = kt % c.cin + lh * 8, ky = kk / 3, kx = kk % 3;
+        va = make_uint4(0u, 0u, 0u, 0u);
+        vb = make_uint4(0u, 0u, 0u, 0u);
+        if (mv) {
+            int iy = oy * c.stride + ky - 1, ix = ox * c.stride + kx - 1;
+            if (iy >= 0 && iy < c.hl && ix >= 0 && ix < c.wl) {
+                if (c.up) { iy >>= 1; ix >>= 1; }
+                va = *reinterpret_cast<const uint4 *>(c.in + (((size_t)bb * c.hin + iy) * c.win + ix) * c.cin + ci);
+            }
+        }
+        if (nv) vb = *reinterpret_cast<const uint4 *>(c.w + (size_t)n * K + kt + lh * 8);
+    };
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+    uint4 va, vb;
+    load(0, va, vb);
+    for (int kt = 0; kt < K; kt += BK) {
+        *reinterpret_cast<uint4 *>(&As[lr][lh * 8]) = va;
+        *reinterpret_cast<uint4 *>(&Bs[lr][lh * 8]) = vb;
+        __syncthreads();
+        if (kt + BK < K) load(kt + BK, va, vb);
+        mma_tile<8>(reinterpret_cast<const uint32_t *>(As), reinterpret_cast<const uint32_t *>(Bs), acc, wm, wn,
+                    lane);
+        __syncthreads();
+    }
+    const int gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int row = m0 + wm * 32 + mi * 16 + gid + (e >= 2 ? 8 : 0);
+                const int col = n0 + wn * 32 + ni * 8 + 2 * tig + (e & 1);
+                if (row >= M || col >= N) continue;
+                float v = acc[mi][ni][e] + c.bias[col];
+                if (c.skip) v += bf2f(c.skip[(size_t)row * N + col]);
+                if (c.relu) v = fmaxf(v, 0.f);
+                if (c.out32) {
+                    if (col < c.out32_ch) c.out32[(size_t)row * c.out32_ch + col] = v;
+                } else {
+                    c.out[(size_t)row * N + col] = f2bf(v);
+                }
+            }
+}
+
+// ---------------------------------------------------------------- data gradient
+
+// dst[b][iy][ix][ci] += sum over (ky, kx, co) of W[co][ky][kx][ci] * dpre[b][oy][ox][co]
+// over the logical input (before any nearest pooling back to the physical input).
+__global__ void __launch_bounds__(GT) k_conv_dgrad(Conv c, const bf16 *dpre, float *dst)
+{
+    __shared__ __align__(16) bf16 As[BM][BK];
+    __shared__ __align__(16) bf16 Bs[BN][BK];
+    const int M = c.B * c.hl * c.wl, N = c.cin, K = 9 * c.cout;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, wm = warp & 1, wn = warp >> 1;
+    const int lr = t >> 1, lh = t & 1;
+    const int m = m0 + lr, n = n0 + lr;
+    const bool mv = m < M, nv = n < N;
+    int bb = 0, iy = 0, ix = 0;
+    if (mv) { ix = m % c.wl; iy = (m / c.wl) % c.hl; bb = m / (c.wl * c.hl); }
+    auto load = [&](int kt, uint4 &va, uint4 &vb) {
+        const int kk = kt / c.cout, co = kt % c.cout + lh * 8, ky = kk / 3, kx = kk % 3;
+        va = make_uint4(0u, 0u, 0u, 0u);
+        vb = make_uint4(0u, 0u, 0u, 0u);
+        if (mv) {
+            const int ny = iy + 1 - ky, nx = ix + 1 - kx;
+            if (ny >= 0 && nx >= 0 && ny % c.stride == 0 && nx % c.stride == 0) {
+                const int oy = ny / c.stride, ox = nx / c.stride;
+                if (oy < c.hout && ox < c.wout)
+                    va = *reinterpret_cast<const uint4 *>(dpre + (((size_t)bb * c.hout + oy) * c.wout + ox) * c.cout +
+                                                          co);
+            }
+        }
+        if (nv) vb = *reinterpret_cast<const uint4 *>(c.wT + (size_t)n * K + kt + lh * 8);
+    };
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+    uint4 va, vb;
+    load(0, va, vb);
+    for (int kt = 0; kt < K; kt += BK) {
+        *reinterpret_cast<uint4 *>(&As[lr][lh * 8]) = va;
+        *reinterpret_cast<uint4 *>(&Bs[lr][lh * 8]) = vb;
+        __syncthreads();
+        if (kt + BK < K) load(kt + BK, va, vb);
+        mma_tile<8>(reinterpret_cast<const uint32_t *>(As), reinterpret_cast<const uint32_t *>(Bs), acc, wm, wn,
+                    lane);
+        __syncthreads();
+    }
+    const int gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int row = m0 + wm * 32 + mi * 16 + gid + (e >= 2 ? 8 : 0);
+                const int col = n0 + wn * 32 + ni * 8 + 2 * tig + (e & 1);
+                if (row < M && col < N) dst[(size_t)row * N + col] += acc[mi][ni][e];
+            }
+}
+
+// ---------------------------------------------------------------- weight gradient
+
+constexpr int WS = 9;   // row stride (32-bit words) of the transposed tiles: 18 BF16
+
+// dW[co][ky][kx][ci] += sum over output pixels of dpre[p][co] * in_logical[p shifted][ci];
+// split over pixel ranges (blockIdx.z), FP32 atomics into dW.
+__global__ void __launch_bounds__(GT) k_conv_wgrad(Conv c, const bf16 *dpre, float *dW, int pix_per_split)
+{
+    __shared__ __align__(16) bf16 As[BM * 2 * WS];
+    __shared__ __align__(16) bf16 Bs[BN * 2 * WS];
+    const int M = c.cout, N = 9 * c.cin, P = c.B * c.hout * c.wout;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int p_begin = blockIdx.z * pix_per_split, p_end = min(P, p_begin + pix_per_split);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, wm = warp & 1, wn = warp >> 1;
+    const int lp = t & 15, c8 = (t >> 4) * 8;        // pixel within the K tile, 8-wide channel group
+    const int n = n0 + c8;
+    const bool nv = n < N;
+    int kk = 0, ci = 0, ky = 0, kx = 0;
+    if (nv) { kk = n / c.cin; ci = n % c.cin; ky = kk / 3; kx = kk % 3; }
+    const int co = m0 + c8;
+    const bool cv = co < M;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+    for (int p0 = p_begin; p0 < p_end; p0 += BK) {
+        const int p = p0 + lp;
+        uint4 va = make_uint4(0u, 0u, 0u, 0u), vb = make_uint4(0u, 0u, 0u, 0u);
+        if (p < p_end) {
+            if (cv) va = *reinterpret_cast<const uint4 *>(dpre + (size_t)p * c.cout + co);
+            if (nv) {
+                const int ox = p % c.wout, oy = (p / c.wout) % c.hout, bb = p / (c.wout * c.hout);
+                int iy = oy * c.stride + ky - 1, ix = ox * c.stride + kx - 1;
+                if (iy >= 0 && iy < c.hl && ix >= 0 && ix < c.wl) {
+                    if (c.up) { iy >>= 1; ix >>= 1; }
+                    vb = *reinterpret_cast<const uint4 *>(c.in + (((size_t)bb * c.hin + iy) * c.win + ix) * c.cin + ci);
+                }
+            }
+        }
+        const bf16 *ea = reinterpret_cast<const bf16 *>(&va), *eb = reinterpret_cast<const bf16 *>(&vb);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            As[(c8 + j) * 2 * WS + lp] = ea[j];
+            Bs[(c8 + j) * 2 * WS + lp] = eb[j];
+        }
+        __syncthreads();
+        mma_tile<WS>(reinterpret_cast<const uint32_t *>(As), reinterpret_cast<const uint32_t *>(Bs), acc, wm, wn,
+                     lane);
+        __syncthreads();
+    }
+    const int gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int row = m0 + wm * 32 + mi * 16 + gid + (e >= 2 ? 8 : 0);
+                const int col = n0 + wn * 32 + ni * 8 + 2 * tig + (e & 1);
+                if (row < M && col < N) atomicAdd(dW + (size_t)row * N + col, acc[mi][ni][e]);
+            }
+}
+
+// ---------------------------------------------------------------- elementwise
+
+__global__ void k_input(const float *x, bf16 *xin, long long npix)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npix * CIN_PAD) return;
+    const long long p = i / CIN_PAD;
+    const int ch = (int)(i % CIN_PAD);
+    xin[i] = f2bf(ch < TSURR_CIN ? x[p * TSURR_CIN + ch] : 0.f);
+}
+
+__global__ void k_mask_sum(const float *mask, long long npix, float *sum)
+{
+    float s = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x)
+        s += mask[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(sum, s);
+}
+
+// loss terms and the output-layer gradient (16 channels, 4 used)
+__global__ void k_loss(const float *y, const float *tgt, const float *mask, const float *msum, long long npix,
+                       bf16 *dpre, double *loss)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.f;
+    if (p < npix) {
+        const float m = mask[p];
+        const float inv = *msum > 0.f ? 1.f / *msum : 0.f;
+        float r[3], e2 = 0.f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) { r[ch] = y[p * 4 + ch] - tgt[p * 3 + ch]; e2 += r[ch] * r[ch]; }
+        const float ri = y[p * 4 + 3] - sqrtf(e2);
+        l = m * (e2 + ri * ri) * inv;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) dpre[p * COUT_PAD + ch] = f2bf(2.f * m * r[ch] * inv);
+        dpre[p * COUT_PAD + 3] = f2bf(2.f * m * ri * inv);
+#pragma unroll
+        for (int ch = 4; ch < COUT_PAD; ++ch) dpre[p * COUT_PAD + ch] = f2bf(0.f);
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss, (double)l);
+}
+
+// gradient at a layer output -> gradient before the ReLU (BF16 for the GEMMs),
+// also added to the gradient of the skip source when the layer has one
+__global__ void k_dpre(const float *d, const bf16 *a, bf16 *dpre, float *skip_grad, long long n, int relu)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float g = d[i];
+    if (relu && !(bf2f(a[i]) > 0.f)) g = 0.f;
+    dpre[i] = f2bf(g);
+    if (skip_grad) skip_grad[i] += g;
+}
+
+// gradient of a nearest x2 upsampling: sum the 2x2 children
+__global__ void k_pool2(const float *src, float *dst, int B, int h, int w, int ch)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)B * h * w * ch;
+    if (i >= n) return;
+    const int c = (int)(i % ch);
+    const long long pix = i / ch;
+    const int x = (int)(pix % w), y = (int)((pix / w) % h), b = (int)(pix / ((long long)w * h));
+    float s = 0.f;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx)
+            s += src[(((long long)b * 2 * h + 2 * y + dy) * 2 * w + 2 * x + dx) * ch + c];
+    dst[i] += s;
+}
+
+__global__ void k_bias_grad(const bf16 *dpre, long long npix, int ch, float *db)
+{
+    const int c = threadIdx.x % ch;
+    const int lanes_per = blockDim.x / ch;
+    const int sub = threadIdx.x / ch;
+    if (sub >= lanes_per) return;
+    float s = 0.f;
+    for (long long p = (long long)blockIdx.x * lanes_per + sub; p < npix; p += (long long)gridDim.x * lanes_per)
+        s += bf2f(dpre[p * ch + c]);
+    atomicAdd(db + c, s);
+}
+
+__global__ void k_adam(float *p, const float *g, float *m1, float *m2, long long n, float lr, float b1, float b2,
+                       float eps, float c1, float c2)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.f - b1) * gi;
+    const float b = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = b;
+    p[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+}
+
+// FP32 master weights -> BF16 [cout][3][3][cin] and the transposed [cin][3][3][cout]
+__global__ void k_weights(const float *w, bf16 *wb, bf16 *wt, int cout, int cin)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cout * 9 * cin) return;
+    const int ci = i % cin, kk = (i / cin) % 9, co = i / (9 * cin);
+    const bf16 v = f2bf(w[i]);
+    wb[i] = v;
+    wt[((size_t)ci * 9 + kk) * cout + co] = v;
+}
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+struct tsurr_net {
+    int maxB = 0, H = 0, W = 0;
+    cudaStream_t s = nullptr;
+    int cin[NL], cout[NL], hin[NL], win[NL], stride[NL], up[NL], relu[NL], skip[NL], src[NL];
+    long long woff[NL], boff[NL];
+    long long nparam = 0;
+    float *p = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;
+    bf16 *wb[NL] = {}, *wt[NL] = {};
+    bf16 *wmem = nullptr;
+    bf16 *act[NL + 1] = {};      // act[0] = padded input, act[i+1] = output of layer i (BF16)
+    float *dact[NL + 1] = {};    // FP32 gradients of act[1..8]
+    float *y = nullptr;          // FP32 network output [B][H][W][4]
+    bf16 *dpre = nullptr;
+    float *dinl = nullptr;
+    float *msum = nullptr;
+    double *loss = nullptr;
+    float *xbuf = nullptr, *tbuf = nullptr, *mbuf = nullptr;
+    std::vector<void *> allocs;
+};
+
+static int sfail(int code, const std::string &m)
+{
+    tsim_record_error(m);
+    return code;
+}
+
+#define SCU(call)                                                                              \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return sfail(TSIM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+
+static long long act_elems(const tsurr_net *n, int i, int B)
+{
+    // i = 0: padded input; i >= 1: output of layer i-1
+    if (i == 0) return (long long)B * n->H * n->W * CIN_PAD;
+    const int L = i - 1;
+    const int hl = n->up[L] ? 2 * n->hin[L] : n->hin[L], wl = n->up[L] ? 2 * n->win[L] : n->win[L];
+    return (long long)B * (hl / n->stride[L]) * (wl / n->stride[L]) * n->cout[L];
+}
+
+static Conv conv_of(const tsurr_net *n, int L, int B)
+{
+    Conv c;
+    memset(&c, 0, sizeof(c));
+    c.in = n->act[n->src[L]];
+    c.B = B;
+    c.hin = n->hin[L];
+    c.win = n->win[L];
+    c.cin = n->cin[L];
+    c.up = n->up[L];
+    c.stride = n->stride[L];
+    c.hl = c.up ? 2 * c.hin : c.hin;
+    c.wl = c.up ? 2 * c.win : c.win;
+    c.hout = c.hl / c.stride;
+    c.wout = c.wl / c.stride;
+    c.cout = n->cout[L];
+    c.w = n->wb[L];
+    c.wT = n->wt[L];
+    c.bias = n->p + n->boff[L];
+    c.skip = n->skip[L] >= 0 ? n->act[n->skip[L]] : nullptr;
+    c.relu = n->relu[L];
+    c.out = n->act[L + 1];
+    c.out32 = nullptr;
+    return c;
+}
+
+extern "C" int tsurr_create(int max_batch, int height, int width, void *stream, tsurr_net **out)
+{
+    if (!out) return sfail(TSIM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (max_batch < 1 || max_batch > 4096 || height < 8 || width < 8 || height % 8 || width % 8 || height > 512 ||
+        width > 512)
+        return sfail(TSIM_ERR_INVALID_ARG, "need 1 <= max_batch <= 4096 and 8 <= H, W <= 512, multiples of 8");
+    tsurr_net *n = new tsurr_net();
+    n->maxB = max_batch;
+    n->H = height;
+    n->W = width;
+    n->s = (cudaStream_t)stream;
+    const int H = height, W = width;
+    // layer table (see tsurr.h)
+    const int ci[NL] = {CIN_PAD, 32, 64, 128, 256, 256, 128, 64, 32};
+    const int co[NL] = {32, 64, 128, 256, 256, 128, 64, 32, COUT_PAD};
+    const int hi[NL] = {H, H, H / 2, H / 4, H / 8, H / 8, H / 4, H / 2, H};
+    const int st[NL] = {1, 2, 2, 2, 1, 1, 1, 1, 1};
+    const int upv[NL] = {0, 0, 0, 0, 0, 1, 1, 1, 0};
+    const int sk[NL] = {-1, -1, -1, -1, -1, 3, 2, 1, -1};   // act index added before the ReLU
+    for (int L = 0; L < NL; ++L) {
+        n->cin[L] = ci[L];
+        n->cout[L] = co[L];
+        n->hin[L] = hi[L];
+        n->win[L] = hi[L] * W / H;
+        n->stride[L] = st[L];
+        n->up[L] = upv[L];
+        n->relu[L] = L < NL - 1;
+        n->skip[L] = sk[L];
+        n->src[L] = L;   // layer L reads act[L]
+        n->woff[L] = n->nparam;
+        n->nparam += (long long)co[L] * 9 * ci[L];
+        n->boff[L] = n->nparam;
+        n->nparam += co[L];
+    }
+    auto alloc = [&](void **p, size_t bytes) -> bool {
+        if (cudaMalloc(p, bytes) != cudaSuccess) return false;
+        n->allocs.push_back(*p);
+        return true;
+    };
+    long long wtotal = 0;
+    for (int L = 0; L < NL; ++L) wtotal += (long long)co[L] * 9 * ci[L];
+    bool ok = alloc((void **)&n->p, n->nparam * 4) && alloc((void **)&n->g, n->nparam * 4) &&
+              alloc((void **)&n->m1, n->nparam * 4) && alloc((void **)&n->m2, n->nparam * 4) &&
+              alloc((void **)&n->wmem, wtotal * 2 * sizeof(bf16));
+    long long wo = 0;
+    for (int L = 0; L < NL && ok; ++L) {
+        n->wb[L] = n->wmem + wo;
+        n->wt[L] = n->wmem + wtotal + wo;
+        wo += (long long)co[L] * 9 * ci[L];
+    }
+    long long maxl = 0;
+    for (int i = 0; i <= NL && ok; ++i) {
+        const long long e = act_elems(n, i, max_batch);
+        ok = alloc((void **)&n->act[i], e * sizeof(bf16));
+        if (ok && i >= 1) ok = alloc((void **)&n->dact[i], e * sizeof(float));
+        if (i >= 1 && e > maxl) maxl = e;
+    }
+    long long maxlogical = 0;
+    for (int L = 0; L < NL; ++L)
+        if (upv[L]) {
+            const long long e = (long long)max_batch * (2 * hi[L]) * (2 * hi[L] * W / H) * ci[L];
+            if (e > maxlogical) maxlogical = e;
+        }
+    const long long npix = (long long)max_batch * H * W;
+    ok = ok && alloc((void **)&n->y, npix * 4 * sizeof(float)) && alloc((void **)&n->dpre, maxl * sizeof(bf16)) &&
+         alloc((void **)&n->dinl, (maxlogical > 0 ? maxlogical : 1) * sizeof(float)) &&
+         alloc((void **)&n->msum, 64) && alloc((void **)&n->loss, 64) &&
+         alloc((void **)&n->xbuf, npix * TSURR_CIN * sizeof(float)) &&
+         alloc((void **)&n->tbuf, npix * 3 * sizeof(float)) && alloc((void **)&n->mbuf, npix * sizeof(float));
+    if (!ok) {
+        cudaGetLastError();
+        for (void *p : n->allocs) cudaFree(p);
+        delete n;
+        return sfail(TSIM_ERR_OOM, "tsurr_create: device allocation failed");
+    }
+    cudaMemsetAsync(n->p, 0, n->nparam * 4, n->s);
+    cudaMemsetAsync(n->g, 0, n->nparam * 4, n->s);
+    cudaMemsetAsync(n->m1, 0, n->nparam * 4, n->s);
+    cudaMemsetAsync(n->m2, 0, n->nparam * 4, n->s);
+    cudaMemsetAsync(n->wmem, 0, wtotal * 2 * sizeof(bf16), n->s);
+    if (cudaStreamSynchronize(n->s) != cudaSuccess) {
+        for (void *p : n->allocs) cudaFree(p);
+        delete n;
+        return sfail(TSIM_ERR_CUDA, "tsurr_create: initialisation failed");
+    }
+    *out = n;
+    return TSIM_OK;
+}
+
+extern "C" void tsurr_destroy(tsurr_net *n)
+{
+    if (!n) return;
+    cudaStreamSynchronize(n->s);
+    for (void *p : n->allocs) cudaFree(p);
+    delete n;
+}
+
+extern "C" int64_t tsurr_num_params(const tsurr_net *n) { return n ? n->nparam : 0; }
+
+static int refresh_weights(tsurr_net *n)
+{
+    for (int L = 0; L < NL; ++L) {
+        const int cnt = n->cout[L] * 9 * n->cin[L];
+        k_weights<<<cdiv(cnt, 256), 256, 0, n->s>>>(n->p + n->woff[L], n->wb[L], n->wt[L], n->cout[L], n->cin[L]);
+    }
+    SCU(cudaGetLastError());
+    return TSIM_OK;
+}
+
+extern "C" int tsurr_set_params(tsurr_net *n, const float *p, int64_t cnt, int on_device)
+{
+    if (!n || !p || cnt != n->nparam) return sfail(TSIM_ERR_INVALID_ARG, "tsurr_set_params: need all parameters");
+    SCU(cudaMemcpyAsync(n->p, p, cnt * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, n->s));
+    SCU(cudaMemsetAsync(n->m1, 0, cnt * 4, n->s));
+    SCU(cudaMemsetAsync(n->m2, 0, cnt * 4, n->s));
+    int rc = refresh_weights(n);
+    if (rc) return rc;
+    SCU(cudaStreamSynchronize(n->s));
+    return TSIM_OK;
+}
+
+extern "C" int tsurr_get_params(tsurr_net *n, float *p, int64_t cnt, int on_device)
+{
+    if (!n || !p || cnt != n->nparam) return sfail(TSIM_ERR_INVALID_ARG, "tsurr_get_params: need all parameters");
+    SCU(cudaMemcpyAsync(p, n->p, cnt * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, n->s));
+    SCU(cudaStreamSynchronize(n->s));
+    return TSIM_OK;
+}
+
+extern "C" int tsurr_get_grads(tsurr_net *n, float *g, int64_t cnt, int on_device)
+{
+    if (!n || !g || cnt != n->nparam) return sfail(TSIM_ERR_INVALID_ARG, "tsurr_get_grads: need all parameters");
+    SCU(cudaMemcpyAsync(g, n->g, cnt * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, n->s));
+    SCU(cudaStreamSynchronize(n->s));
+    return TSIM_OK;
+}
+
+static int run_forward(tsurr_net *n, const float *x, int B)
+{
+    const long long npix = (long long)B * n->H * n->W;
+    k_input<<<cdiv(npix * CIN_PAD, 256), 256, 0, n->s>>>(x, n->act[0], npix);
+    for (int L = 0; L < NL; ++L) {
+        Conv c = conv_of(n, L, B);
+        if (L == NL - 1) {
+            c.out = nullptr;
+            c.out32 = n->y;
+            c.out32_ch = TSURR_COUT;
+        }
+        dim3 grid(cdiv((long long)B * c.hout * c.wout, BM), cdiv(c.cout, BN));
+        k_conv_fwd<<<grid, GT, 0, n->s>>>(c);
+    }
+    SCU(cudaGetLastError());
+    return TSIM_OK;
+}
+
+static const float *stage(tsurr_net *n, const float *src, float *buf, size_t bytes, int on_device, int *rc)
+{
+    *rc = TSIM_OK;
+    if (on_device) return src;
+    if (cudaMemcpyAsync(buf, src, bytes, cudaMemcpyHostToDevice, n->s) != cudaSuccess)
+        *rc = sfail(TSIM_ERR_CUDA, "tsurr: host to device copy failed");
+    return buf;
+}
+
+extern "C" int tsurr_forward(tsurr_net *n, const float *x, int B, float *y, int on_device)
+{
+    if (!n || !x || !y || B < 1 || B > n->maxB) return sfail(TSIM_ERR_INVALID_ARG, "tsurr_forward: bad arguments");
+    const long long npix = (long long)B * n->H * n->W;
+    int rc;
+    const float *xd = stage(n, x, n->xbuf, npix * TSURR_CIN * 4, on_device, &rc);
+    if (rc) return rc;
+    rc = run_forward(n, xd, B);
+    if (rc) return rc;
+    SCU(cudaMemcpyAsync(y, n->y, npix * 4 * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        n->s));
+    if (!on_device) SCU(cudaStreamSynchronize(n->s));
+    return TSIM_OK;
+}
+
+extern "C" int tsurr_backward(tsurr_net *n, const float *x, const float *target, const float *mask, int B,
+                              double *loss, int on_device)
+{
+    if (!n || !x || !target || !mask || B < 1 || B > n->maxB)
+        return sfail(TSIM_ERR_INVALID_ARG, "tsurr_backward: bad arguments");
+    const long long npix = (long long)B * n->H * n->W;
+    int rc;
+    const float *xd = stage(n, x, n->xbuf, npix * TSURR_CIN * 4, on_device, &rc);
+    if (rc) return rc;
+    const float *td = stage(n, target, n->tbuf, npix * 3 * 4, on_device, &rc);
+    if (rc) return rc;
+    const float *md = stage(n, mask, n->mbuf, npix * 4, on_device, &rc);
+    if (rc) return rc;
+    rc = run_forward(n, xd, B);
+    if (rc) return rc;
+    SCU(cudaMemsetAsync(n->g, 0, n->nparam * 4, n->s));
+    SCU(cudaMemsetAsync(n->msum, 0, 64, n->s));
+    SCU(cudaMemsetAsync(n->loss, 0, 64, n->s));
+    for (int i = 1; i <= NL; ++i) SCU(cudaMemsetAsync(n->dact[i], 0, act_elems(n, i, B) * sizeof(float), n->s));
+    k_mask_sum<<<256, 256, 0, n->s>>>(md, npix, n->msum);
+    // output layer: gradient of the loss w.r.t. its (pre-activation) output
+    k_loss<<<cdiv(npix, 256), 256, 0, n->s>>>(n->y, td, md, n->msum, npix, n->dpre, n->loss);
+    for (int L = NL - 1; L >= 0; --L) {
+        Conv c = conv_of(n, L, B);
+        const long long nout = (long long)B * c.hout * c.wout * c.cout;
+        if (L < NL - 1) {
+            float *skipg = n->skip[L] >= 0 ? n->dact[n->skip[L]] : nullptr;
+            k_dpre<<<cdiv(nout, 256), 256, 0, n->s>>>(n->dact[L + 1], n->act[L + 1], n->dpre, skipg, nout, 1);
+        }
+        // weight and bias gradients
+        const long long P = (long long)B * c.hout * c.wout;
+        const int splits = (int)std::max<long long>(1, std::min<long long>(256, P / 2048));
+        int pps = (int)((P + splits - 1) / splits);
+        pps = (pps + BK - 1) / BK * BK;
+        dim3 gw(cdiv(c.cout, BM), cdiv(9LL * c.cin, BN), cdiv(P, pps));
+        k_conv_wgrad<<<gw, GT, 0, n->s>>>(c, n->dpre, n->g + n->woff[L], pps);
+        k_bias_grad<<<128, 256, 0, n->s>>>(n->dpre, P, c.cout, n->g + n->boff[L]);
+        // data gradient towards the layer input (not needed for the network input)
+        if (L > 0) {
+            dim3 gd(cdiv((long long)B * c.hl * c.wl, BM), cdiv(c.cin, BN));
+            if (c.up) {
+                SCU(cudaMemsetAsync(n->dinl, 0, (size_t)B * c.hl * c.wl * c.cin * sizeof(float), n->s));
+                k_conv_dgrad<<<gd, GT, 0, n->s>>>(c, n->dpre, n->dinl);
+                const long long nin = (long long)B * c.hin * c.win * c.cin;
+                k_pool2<<<cdiv(nin, 256), 256, 0, n->s>>>(n->dinl, n->dact[L], B, c.hin, c.win, c.cin);
+            } else {
+                k_conv_dgrad<<<gd, GT, 0, n->s>>>(c, n->dpre, n->dact[L]);
+            }
+        }
+    }
+    SCU(cudaGetLastError());
+    double l = 0.0;
+    SCU(cudaMemcpyAsync(&l, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->s));
+    SCU(cudaStreamSynchronize(n->s));
+    if (loss) *loss = l;
+    return TSIM_OK;
+}
+
+extern "C" int tsurr_adam(tsurr_net *n, float lr, float b1, float b2, float eps, int t)
+{
+    if (!n || t < 1 || !(lr > 0.f) || !(b1 >= 0.f && b1 < 1.f) || !(b2 >= 0.f && b2 < 1.f) || !(eps > 0.f))
+        return sfail(TSIM_ERR_INVALID_ARG, "tsurr_adam: bad arguments");
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    k_adam<<<cdiv(n->nparam, 256), 256, 0, n->s>>>(n->p, n->g, n->m1, n->m2, n->nparam, lr, b1, b2, eps, c1, c2);
+    return refresh_weights(n);
+}

@@ -86,3 +86,36 @@ def test_descriptors_from_inputs():
     for cx in (5, 13, 31):
         nx, ny, nz = I.Gel(cx, cx + 2, 3, 1e-3).nodes
         assert nx % 4 == 0 and ny % 4 == 0 and nz % 4 == 0 and nx >= cx + 8
+
+
+def test_surrogate_header_symbols_exported():
+    from paper_2405_02914_gb300 import tsurr
+    src = open(os.path.join(ROOT, "include", "tsurr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = sorted(set(re.findall(r"\b(tsurr_[a-z0-9_]+)\s*\(", src)))
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (tsurr_[a-z0-9_]+)$", out, flags=re.M))
+    assert names and not [n for n in names if n not in exported]
+    assert set(names) == set(tsurr.EXPORTS)
+    tsurr.load()
+
+
+def test_surrogate_invalid_arguments_rejected_without_gpu():
+    from paper_2405_02914_gb300 import tsurr
+    L = tsurr.load()
+    out = C.c_void_p()
+    assert L.tsurr_create(4, 12, 16, None, C.byref(out)) == 1          # not a multiple of 8
+    assert out.value is None
+    assert L.tsurr_create(0, 16, 16, None, C.byref(out)) == 1
+    assert L.tsurr_forward(None, None, 1, None, 1) == 1
+    assert L.tsurr_backward(None, None, None, None, 1, None, 1) == 1
+    assert L.tsurr_adam(None, 1e-3, 0.9, 0.999, 1e-8, 1) == 1
+    assert L.tsurr_num_params(None) == 0
+    L.tsurr_destroy(None)
+
+
+def test_surrogate_layer_table_matches_inputs():
+    from paper_2405_02914_gb300 import inputs as I
+    from paper_2405_02914_gb300 import tsurr
+    assert [(a, b) for a, b, *_ in tsurr.LAYERS] == I.SURR_CONVS
+    assert tsurr.num_params() == I.surrogate_params(0).size == 1374160
