@@ -171,6 +171,49 @@ def run_reference(args, scene):
     print(json.dumps(line), flush=True)
 
 
+SURROGATE_WEIGHTS = os.path.join(ROOT, "paper_2405_02914_gb300", "weights", "surrogate_pad64.npz")
+
+
+def surrogate_leg(n_traj=8, threshold=0.02):
+    """Surrogate vs IMPM surface frames/s on held-out trajectories of the
+    surrogate's pad (64x64x16 cells, 128x128 frames at dx/2 pitch every 100
+    substeps): IMPM frames/s measured on the frames it makes here, network
+    frames/s at inference batch 256 on device-resident inputs, per-frame error
+    against those IMPM frames, and the frames/s served when frames whose
+    predicted error exceeds ``threshold`` x press depth fall back to IMPM."""
+    if not os.path.exists(SURROGATE_WEIGHTS):
+        return {"unavailable": "no trained parameters at %s" % os.path.relpath(SURROGATE_WEIGHTS, ROOT)}
+    import numpy as np
+    from paper_2405_02914_gb300 import inputs as I
+    from paper_2405_02914_gb300 import surrogate as G
+    params, meta = G.load_params(SURROGATE_WEIGHTS)
+    fr = G.generate(I.surrogate_scenes(n_traj, seed=1))
+    mpm_fps = fr.mpm_frames / fr.mpm_seconds
+    pred = G.predict(params, fr)
+    err = G.frame_errors(pred, fr)
+    ind = G.indicator(pred, fr)
+    del pred
+    summ = G.serve_summary(err, ind, threshold)
+    t_batch = G.time_inference(params, batch=256)
+    surr_fps = 256 / t_batch
+    n_fb = summ["fallback_frac"] * len(fr)
+    served = len(fr) / (len(fr) / surr_fps + n_fb / mpm_fps)
+    tflops = G.forward_flops() * 256 / t_batch / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, src = float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, src = 1900.0, "fallback"
+    return {"frames_per_s": surr_fps, "mpm_frames_per_s": mpm_fps, "served_frames_per_s": served,
+            "speedup_served": served / mpm_fps, "speedup_network": surr_fps / mpm_fps,
+            "threshold": threshold, "frames": len(fr), "trajectories": n_traj, **summ,
+            "inference_batch": 256, "frame": "128x128x3 displacement + indicator",
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "peak_source": src,
+                         "kernel": "k_conv_fwd (mma.sync m16n8k16 BF16, FP32 accumulate), whole forward"},
+            "weights": os.path.relpath(SURROGATE_WEIGHTS, ROOT), "trained": meta}
+
+
 def workload(name, seed):
     """Scenes of a named workload and its description."""
     from paper_2405_02914_gb300 import inputs as I
@@ -196,6 +239,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="pad4m", choices=["pad4m", "press65k", "batch64", "large33m"])
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate vs IMPM frames/s leg")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch kernels one by one (profilers cannot see inside graphs with loops)")
     args = ap.parse_args()
@@ -338,8 +382,7 @@ def main():
                    "particle_substeps_per_s": n * substeps * world / (t_max * 1e-3),
                    "substep_ms": t_max / max(substeps, 1),
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (particle state %d MB per parity)" % (n * 52 // 2 ** 20),
-                   "surrogate_frames_per_s": None},
+                   "l2": "inputs larger than L2 (particle state %d MB per parity)" % (n * 52 // 2 ** 20)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _traffic(n),
                      "kernel": "k_transfer<COMMIT> (fused G2P -> F,x move -> re-bin -> P2G)",
@@ -357,6 +400,11 @@ def main():
     line["gpu_launches"] = int(4 * substeps + 3 * extra + 3 * args.steps * len(scenes)) * world
     if args.workload != "pad4m":
         line["metric"] = UNIT + " (%s)" % args.workload
+    if not args.no_surrogate and world == 1:
+        try:
+            line["surrogate"] = surrogate_leg()
+        except Exception as e:          # reported, never silently replaced by another path
+            line["surrogate"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene)
     print(json.dumps(line), flush=True)

@@ -29,6 +29,10 @@
  *
  * Conventions as in tsim.h: int status codes (TSIM_*), tsim_last_error()
  * for the reason, the caller's stream, no allocation after tsurr_create.
+ *
+ * Kernels: the forward convolutions run on the tcgen05 tensor cores (UMMA
+ * M = 128 pixels x N = cout, accumulators in tensor memory); the data- and
+ * weight-gradient convolutions on mma.sync m16n8k16.
  */
 #ifndef TSURR_H
 #define TSURR_H
@@ -66,6 +70,12 @@ int tsurr_forward(tsurr_net *net, const float *x, int batch, float *y, int on_de
  * mask[B,H,W]; gradients go to the internal buffer; *loss (host) = L. */
 int tsurr_backward(tsurr_net *net, const float *x, const float *target, const float *mask, int batch,
                    double *loss, int on_device);
+
+/* Wait for the network's work on its stream; returns TSIM_ERR_TIMEOUT if a
+ * bounded pipeline wait inside a kernel gave up (latched until destroy).
+ * tsurr_forward with device pointers does not wait: call this to see such
+ * errors; host-pointer calls and tsurr_backward check them themselves. */
+int tsurr_sync(tsurr_net *net);
 
 /* One Adam step (bias-corrected, step t >= 1) on all parameters. */
 int tsurr_adam(tsurr_net *net, float lr, float beta1, float beta2, float eps, int t);

@@ -80,68 +80,238 @@ struct Conv {
     int out32_ch;
 };
 
-// ---------------------------------------------------------------- forward
+// ---------------------------------------------------------------- forward on tcgen05
 
-__global__ void __launch_bounds__(GT) k_conv_fwd(Conv c)
+// The forward runs on the 5th-generation tensor cores: one CTA computes 128
+// output pixels x all cout channels, D[128][cout] in tensor memory (TMEM).
+// Operands are staged in shared memory by cp.async (the im2col gather with
+// zero fill for the padding), in the no-swizzle K-major layout of 8-row x
+// 16-byte core matrices; one elected thread issues tcgen05.mma (M = 128,
+// N = cout, K = 16) and tracks completion with tcgen05.commit on a per-stage
+// mbarrier; the epilogue reads D back with tcgen05.ld (warp w owns TMEM lanes
+// 32w..32w+31, i.e. its 32 pixels) and fuses bias, skip and ReLU.
+constexpr int TC_M = 128;          // output pixels per CTA (UMMA M)
+constexpr int TC_STAGES = 4;       // shared-memory stages of 64 K each (4 UMMAs of K = 16)
+constexpr int TC_DIST = 2;         // k-tiles loaded ahead of the one being multiplied
+constexpr uint32_t TC_LBO = 128;   // bytes between the two K halves (core matrices) of a K16 slice
+constexpr uint32_t TC_SBO = 256;   // bytes between 8-row groups of a K16 slice
+constexpr int TC_WAIT = 1 << 22;   // polls before a wait gives up
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t bytes)
 {
-    __shared__ __align__(16) bf16 As[BM][BK];
-    __shared__ __align__(16) bf16 Bs[BN][BK];
-    const int M = c.B * c.hout * c.wout, N = c.cout, K = 9 * c.cin;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, wm = warp & 1, wn = warp >> 1;
-    const int lr = t >> 1, lh = t & 1;
-    const int m = m0 + lr, n = n0 + lr;
-    const bool mv = m < M, nv = n < N;
-    int bb = 0, oy = 0, ox = 0;
-    if (mv) { ox = m % c.wout; oy = (m / c.wout) % c.hout; bb = m / (c.wout * c.hout); }
-    auto load = [&](int kt, uint4 &va, uint4 &vb) {
-        const int kk = kt / c.cin, ci = kt % c.cin + lh * 8, ky = kk / 3, kx = kk % 3;
-        va = make_uint4(0u, 0u, 0u, 0u);
-        vb = make_uint4(0u, 0u, 0u, 0u);
-        if (mv) {
-            int iy = oy * c.stride + ky - 1, ix = ox * c.stride + kx - 1;
-            if (iy >= 0 && iy < c.hl && ix >= 0 && ix < c.wl) {
-                if (c.up) { iy >>= 1; ix >>= 1; }
-                va = *reinterpret_cast<const uint4 *>(c.in + (((size_t)bb * c.hin + iy) * c.win + ix) * c.cin + ci);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void bar_init(uint32_t bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int it = 0; it < TC_WAIT; ++it) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets in 16-byte units, descriptor version 1 (bits 46-48 = 0b001), no
+// swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(TC_LBO >> 4) << 16) | ((uint64_t)(TC_SBO >> 4) << 32) |
+           (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.
+__device__ __forceinline__ uint32_t umma_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                 "[%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// dynamic shared memory of k_conv_fwd_tc for cout channels
+__host__ __device__ inline uint32_t tc_stage_bytes(int cout) { return 4u * (TC_M * 32u + (uint32_t)cout * 32u); }
+__host__ __device__ inline uint32_t tc_smem_bytes(int cout) { return TC_STAGES * tc_stage_bytes(cout) + 1024 + 64; }
+
+__global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(Conv c, int *err)
+{
+    extern __shared__ unsigned char tc_raw[];
+    const int N = c.cout, K = 9 * c.cin, M = c.B * c.hout * c.wout;
+    const int nk16 = K / 16, nkt = (nk16 + 3) / 4;
+    const uint32_t a_bytes = TC_M * 32, b_bytes = (uint32_t)N * 32, stage_bytes = tc_stage_bytes(N);
+    // stages 1024-byte aligned; barriers and the TMEM address after them
+    const uint32_t raw = saddr(tc_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *stages = tc_raw + (base - raw);
+    const uint32_t bars = base + TC_STAGES * stage_bytes;           // TC_STAGES x 8 bytes
+    const uint32_t tslot = bars + 8 * TC_STAGES;
+    uint32_t *tslot_p = reinterpret_cast<uint32_t *>(stages + TC_STAGES * stage_bytes + 8 * TC_STAGES);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int m0 = blockIdx.x * TC_M;
+    const uint32_t ncols = N < 32 ? 32u : (uint32_t)N;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) bar_init(bars + 8 * s);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot_p;
+
+    // loader: thread t moves 16-byte chunk q = t & 7 of rows (t >> 3) + 16 i;
+    // chunk q is K half (q & 1) of K16 slice (q >> 1) of the stage
+    const int q = t & 7, slice = q >> 1, half = q & 1, r0 = t >> 3;
+    int rb[8], ry[8], rx[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = m0 + r0 + 16 * i;
+        if (m < M) {
+            rx[i] = m % c.wout;
+            ry[i] = (m / c.wout) % c.hout;
+            rb[i] = m / (c.wout * c.hout);
+        } else {
+            rb[i] = -1;
+            ry[i] = rx[i] = 0;
+        }
+    }
+    auto load_tile = [&](int kt, int s) {
+        const int k16 = kt * 4 + slice;
+        if (k16 >= nk16) return;
+        const int k = k16 * 16 + half * 8;
+        const int kk = k / c.cin, ci = k % c.cin, ky = kk / 3, kx = kk % 3;
+        const uint32_t sa = saddr(stages + s * stage_bytes) + slice * a_bytes + half * 128;
+        const uint32_t sb = saddr(stages + s * stage_bytes) + 4 * a_bytes + slice * b_bytes + half * 128;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = r0 + 16 * i;
+            int iy = ry[i] * c.stride + ky - 1, ix = rx[i] * c.stride + kx - 1;
+            const bool v = rb[i] >= 0 && iy >= 0 && iy < c.hl && ix >= 0 && ix < c.wl;
+            if (c.up) { iy >>= 1; ix >>= 1; }
+            const bf16 *src = v ? c.in + (((size_t)rb[i] * c.hin + iy) * c.win + ix) * c.cin + ci : c.in;
+            cp_async16(sa + (r >> 3) * TC_SBO + (r & 7) * 16, src, v ? 16u : 0u);
+        }
+        for (int n = r0; n < N; n += 16)
+            cp_async16(sb + (n >> 3) * TC_SBO + (n & 7) * 16, c.w + (size_t)n * K + k, 16u);
+    };
+
+    const uint32_t idesc = umma_idesc(TC_M, N);
+    bool ok = true;
+    for (int j = 0; j < TC_DIST; ++j) {
+        if (j < nkt) load_tile(j, j);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < nkt; ++kt) {
+        const int nx = kt + TC_DIST;
+        if (nx < nkt) {
+            const int s = nx % TC_STAGES;
+            // the stage was last read by the UMMAs of k-tile nx - TC_STAGES
+            if (nx >= TC_STAGES && ok) ok = bar_wait(bars + 8 * s, ((nx - TC_STAGES) / TC_STAGES) & 1);
+            if (ok) load_tile(nx, s);
+        }
+        cp_async_commit();
+        cp_async_wait<TC_DIST>();
+        fence_proxy_async();
+        ok = __syncthreads_and(ok);
+        if (t == 0 && ok) {
+            tc_fence_after();
+            const int s = kt % TC_STAGES;
+            const uint32_t sa = saddr(stages + s * stage_bytes), sb = sa + 4 * a_bytes;
+            for (int j = 0; j < 4 && kt * 4 + j < nk16; ++j)
+                umma_bf16(tmem, umma_desc(sa + j * a_bytes), umma_desc(sb + j * b_bytes), idesc, (kt | j) != 0);
+            umma_commit(bars + 8 * s);
+        }
+    }
+    if (ok) ok = bar_wait(bars + 8 * ((nkt - 1) % TC_STAGES), ((nkt - 1) / TC_STAGES) & 1);
+    cp_async_wait<0>();
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            if (row >= M) continue;
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) + c.bias[c0 + j];
+            if (c.skip) {
+                const uint4 *sp = reinterpret_cast<const uint4 *>(c.skip + (size_t)row * N + c0);
+                uint4 s2[2] = {sp[0], sp[1]};
+                const bf16 *se = reinterpret_cast<const bf16 *>(s2);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] += bf2f(se[j]);
+            }
+            if (c.relu) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+            }
+            if (c.out32) {
+                for (int j = 0; j < 16 && c0 + j < c.out32_ch; ++j) c.out32[(size_t)row * c.out32_ch + c0 + j] = v[j];
+            } else {
+                uint4 o2[2];
+                bf16 *oe = reinterpret_cast<bf16 *>(o2);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) oe[j] = f2bf(v[j]);
+                uint4 *op = reinterpret_cast<uint4 *>(c.out + (size_t)row * N + c0);
+                op[0] = o2[0];
+                op[1] = o2[1];
             }
         }
-        if (nv) vb = *reinterpret_cast<const uint4 *>(c.w + (size_t)n * K + kt + lh * 8);
-    };
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
-    uint4 va, vb;
-    load(0, va, vb);
-    for (int kt = 0; kt < K; kt += BK) {
-        *reinterpret_cast<uint4 *>(&As[lr][lh * 8]) = va;
-        *reinterpret_cast<uint4 *>(&Bs[lr][lh * 8]) = vb;
-        __syncthreads();
-        if (kt + BK < K) load(kt + BK, va, vb);
-        mma_tile<8>(reinterpret_cast<const uint32_t *>(As), reinterpret_cast<const uint32_t *>(Bs), acc, wm, wn,
-                    lane);
-        __syncthreads();
     }
-    const int gid = lane >> 2, tig = lane & 3;
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int row = m0 + wm * 32 + mi * 16 + gid + (e >= 2 ? 8 : 0);
-                const int col = n0 + wn * 32 + ni * 8 + 2 * tig + (e & 1);
-                if (row >= M || col >= N) continue;
-                float v = acc[mi][ni][e] + c.bias[col];
-                if (c.skip) v += bf2f(c.skip[(size_t)row * N + col]);
-                if (c.relu) v = fmaxf(v, 0.f);
-                if (c.out32) {
-                    if (col < c.out32_ch) c.out32[(size_t)row * c.out32_ch + col] = v;
-                } else {
-                    c.out[(size_t)row * N + col] = f2bf(v);
-                }
-            }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    if (t == 0 && !ok) atomicOr(err, 1);
 }
 
 // ---------------------------------------------------------------- data gradient
@@ -401,6 +571,7 @@ struct tsurr_net {
     float *msum = nullptr;
     double *loss = nullptr;
     float *xbuf = nullptr, *tbuf = nullptr, *mbuf = nullptr;
+    int *err = nullptr;          // set by a kernel whose bounded wait gave up
     std::vector<void *> allocs;
 };
 
@@ -521,7 +692,8 @@ extern "C" int tsurr_create(int max_batch, int height, int width, void *stream, 
          alloc((void **)&n->dinl, (maxlogical > 0 ? maxlogical : 1) * sizeof(float)) &&
          alloc((void **)&n->msum, 64) && alloc((void **)&n->loss, 64) &&
          alloc((void **)&n->xbuf, npix * TSURR_CIN * sizeof(float)) &&
-         alloc((void **)&n->tbuf, npix * 3 * sizeof(float)) && alloc((void **)&n->mbuf, npix * sizeof(float));
+         alloc((void **)&n->tbuf, npix * 3 * sizeof(float)) && alloc((void **)&n->mbuf, npix * sizeof(float)) &&
+         alloc((void **)&n->err, 64);
     if (!ok) {
         cudaGetLastError();
         for (void *p : n->allocs) cudaFree(p);
@@ -533,7 +705,10 @@ extern "C" int tsurr_create(int max_batch, int height, int width, void *stream, 
     cudaMemsetAsync(n->m1, 0, n->nparam * 4, n->s);
     cudaMemsetAsync(n->m2, 0, n->nparam * 4, n->s);
     cudaMemsetAsync(n->wmem, 0, wtotal * 2 * sizeof(bf16), n->s);
-    if (cudaStreamSynchronize(n->s) != cudaSuccess) {
+    cudaMemsetAsync(n->err, 0, 64, n->s);
+    if (cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(256)) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(n->s) != cudaSuccess) {
         for (void *p : n->allocs) cudaFree(p);
         delete n;
         return sfail(TSIM_ERR_CUDA, "tsurr_create: initialisation failed");
@@ -601,10 +776,20 @@ static int run_forward(tsurr_net *n, const float *x, int B)
             c.out32 = n->y;
             c.out32_ch = TSURR_COUT;
         }
-        dim3 grid(cdiv((long long)B * c.hout * c.wout, BM), cdiv(c.cout, BN));
-        k_conv_fwd<<<grid, GT, 0, n->s>>>(c);
+        const unsigned grid = cdiv((long long)B * c.hout * c.wout, TC_M);
+        k_conv_fwd_tc<<<grid, 128, tc_smem_bytes(c.cout), n->s>>>(c, n->err);
     }
     SCU(cudaGetLastError());
+    return TSIM_OK;
+}
+
+// latched device errors (a bounded wait that gave up); synchronises
+static int check_err(tsurr_net *n)
+{
+    int e = 0;
+    SCU(cudaMemcpyAsync(&e, n->err, sizeof(int), cudaMemcpyDeviceToHost, n->s));
+    SCU(cudaStreamSynchronize(n->s));
+    if (e) return sfail(TSIM_ERR_TIMEOUT, "tsurr: a tensor-core pipeline wait gave up");
     return TSIM_OK;
 }
 
@@ -628,8 +813,13 @@ extern "C" int tsurr_forward(tsurr_net *n, const float *x, int B, float *y, int 
     if (rc) return rc;
     SCU(cudaMemcpyAsync(y, n->y, npix * 4 * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         n->s));
-    if (!on_device) SCU(cudaStreamSynchronize(n->s));
-    return TSIM_OK;
+    return on_device ? TSIM_OK : check_err(n);
+}
+
+extern "C" int tsurr_sync(tsurr_net *n)
+{
+    if (!n) return sfail(TSIM_ERR_INVALID_ARG, "tsurr_sync: net is NULL");
+    return check_err(n);
 }
 
 extern "C" int tsurr_backward(tsurr_net *n, const float *x, const float *target, const float *mask, int B,
@@ -685,7 +875,8 @@ extern "C" int tsurr_backward(tsurr_net *n, const float *x, const float *target,
     SCU(cudaGetLastError());
     double l = 0.0;
     SCU(cudaMemcpyAsync(&l, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->s));
-    SCU(cudaStreamSynchronize(n->s));
+    rc = check_err(n);
+    if (rc) return rc;
     if (loss) *loss = l;
     return TSIM_OK;
 }

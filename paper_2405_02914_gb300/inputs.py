@@ -156,6 +156,7 @@ class Scene:
     readout_pitch: float = 0.0
     n_substeps: int = 0
     name: str = ""
+    meta: dict = dataclasses.field(default_factory=dict)
 
 
 # ---------------------------------------------------------------- particles
@@ -434,3 +435,67 @@ def surrogate_batch(seed: int, B: int, H: int, W: int, mask_frac: float = 0.8):
     my, mx = int(round(H * (1 - mask_frac) / 2)), int(round(W * (1 - mask_frac) / 2))
     m[:, my:H - my, mx:W - mx] = 1.0
     return x, t, m
+
+
+# surrogate dataset pads: 64 x 64 x 16 cells at dx = 0.3125 mm (20 x 20 x 5 mm,
+# 524,288 particles); a 128 x 128 pixel window at pitch dx/2 is the whole pad
+SURR_PAD = (64, 64, 16)
+SURR_DX = 0.3125e-3
+SURR_PX = 128
+SURR_PHASES = (800, 2400, 2000)      # substeps of the press, slip and rotate phases
+
+
+def surrogate_scenes(n: int, seed: int, first: int = 0) -> List[Scene]:
+    """Trajectories ``first .. first+n-1`` of the seeded surrogate dataset
+    (seed picks the split: training and held-out sets use different seeds).
+    Each draws E in [0.8,3]e5 Pa, nu in [0.40,0.47], mu in [0.2,1.0], an
+    indenter from {sphere r 3-5 mm, cylinder r 2-3 mm, prism side 4-6 mm,
+    Perlin plate 8 x 8 mm, amplitude 0.3 mm} (edges rounded to 2 dx),
+    press 0.3-1.0 mm, slip 0-3 mm in
+    a random direction and rotation of -45..45 deg, over fixed phase lengths
+    so that every trajectory of a batch has the same substep count.  All pads
+    share one particle lattice (gel seed 0) so one reference configuration
+    serves all."""
+    cx, cy, cz = SURR_PAD
+    dx = SURR_DX
+    gel = Gel(cx, cy, cz, dx, seed=0)
+    L = cx * dx
+    # common step from the stiffest material of the ranges (CFL 0.3); flat
+    # punches into gels with nu = 0.48 at CFL 0.4 inverted cells within the
+    # press phase, so nu stops at 0.47 here
+    E, nu = 3e5, 0.47
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    G = E / (2 * (1 + nu))
+    dt = 0.3 * dx / math.sqrt((lam + 2 * G) / 1100.0)
+    n_press, n_slip, n_rot = SURR_PHASES
+    out = []
+    for k in range(first, first + n):
+        rng = np.random.Generator(np.random.Philox(key=0x5C3A + 7919 * seed + k))
+        Em = float(rng.uniform(0.8e5, 3e5))
+        num = float(rng.uniform(0.40, 0.47))
+        mu = float(rng.uniform(0.2, 1.0))
+        kind = int(rng.integers(0, 4))
+        press = float(rng.uniform(0.3e-3, 1.0e-3))
+        slip = float(rng.uniform(0.0, 3e-3))
+        ang = float(rng.uniform(0.0, 2 * math.pi))
+        rot = math.radians(float(rng.uniform(-45.0, 45.0)))
+        # edges rounded to 2 dx: a sharper rim under a nearly incompressible gel
+        # (nu -> 0.48) with sticking friction inverted cells in early runs
+        rnd = 2.0 * dx
+        if kind == 0:
+            ind = sphere(float(rng.uniform(3e-3, 5e-3)), mu)
+        elif kind == 1:
+            ind = cylinder(float(rng.uniform(2e-3, 3e-3)), 10e-3, rnd, mu)
+        elif kind == 2:
+            ind = prism(float(rng.uniform(4e-3, 6e-3)), float(rng.uniform(6e-3, 10e-3)), rnd, mu)
+        else:
+            ind = perlin_plate(4e-3, 4e-3, 1e-3, rnd, 0.3e-3, 4e-3, 0.5, 4, mu, seed=7919 * seed + k)
+        gap = 0.37 * dx
+        d = (math.cos(ang), math.sin(ang))
+        tip0 = (L / 2 - 0.5 * slip * d[0], L / 2 - 0.5 * slip * d[1], gel.height + gap)
+        kf = press_slip_rotate(tip0, press + gap, slip, rot, n_press, n_slip, n_rot, slip_dir=d)
+        meta = dict(press=press, gap=gap, slip=slip, slip_dir=d, rotate=rot, E=Em, nu=num, mu=mu, kind=kind)
+        out.append(Scene(gel, Material(E=Em, nu=num), ind, kf, Solver(dt=dt), readout_every=100,
+                         readout_px=SURR_PX, readout_pitch=dx / 2, n_substeps=n_press + n_slip + n_rot,
+                         name="surrogate", meta=meta))
+    return out

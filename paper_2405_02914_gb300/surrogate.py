@@ -1,0 +1,334 @@
+"""Learned surface surrogate around the IMPM simulator.
+
+* ``generate``: runs seeded trajectories through the batched IMPM (one
+  context, many instances, CUDA-graph stepping) and records, every
+  ``every`` substeps, the indenter heightmap (tsim_read_indenter_height) and
+  the surface displacement field (tsim_read_displacement) on a 128 x 128
+  pixel window at dx/2 pitch, plus the pose and material scalars of the
+  frame.  The frames stay on the device.
+* ``features``: the network input of a set of frames, x[B,H,W,12] =
+  [heightmap, pixel x, pixel y, press depth, slip x, slip y, rotation,
+  E, nu, mu, tip x, tip y] (lengths in mm, scalars broadcast).
+* ``train``: Adam on the masked displacement loss with the residual
+  indicator channel (include/tsurr.h), all in the library's kernels.
+* ``evaluate`` / ``serve``: per-frame error against the IMPM frames,
+  the predicted error from the indicator channel, and the fallback rule:
+  a frame whose predicted RMS error exceeds ``threshold`` x press depth is
+  served by the simulator instead.
+* ``foil``: a no-learning predictor (the penetration of the indenter into
+  the undeformed surface, Gaussian-smoothed, as a vertical displacement)
+  that the trained network is compared against.
+
+The paper has no learned component; this is a project addition.  PyTorch
+only holds device memory and assembles batches.
+"""
+from __future__ import annotations
+
+import dataclasses
+import json
+import math
+import re
+import time
+
+import numpy as np
+
+from . import inputs as I
+from . import tsim as T
+from . import tsurr as S
+
+MM = 1e-3
+CLIP = 2e-3            # heightmap clip (m): columns that miss the indenter read +2 mm
+N_SCALARS = 9          # per-frame scalars broadcast as channels 3..11
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the surrogate pipeline needs a CUDA device")
+    return torch
+
+
+def trajectory_state(kf: np.ndarray, k: float):
+    """Tip (3) and yaw of the piecewise-linear keyframe trajectory at substep k."""
+    kf = np.asarray(kf, np.float64)
+    s = kf[:, 0]
+    if k <= s[0]:
+        row = kf[0, 1:]
+    elif k >= s[-1]:
+        row = kf[-1, 1:]
+    else:
+        j = int(np.searchsorted(s, k, side="right")) - 1
+        a = (k - s[j]) / (s[j + 1] - s[j])
+        row = (1 - a) * kf[j, 1:] + a * kf[j + 1, 1:]
+    return row[:3], row[3]
+
+
+def frame_scalars(scene: I.Scene, k: int) -> np.ndarray:
+    """[press depth, slip x, slip y, rotation, E, nu, mu, tip x, tip y] at substep k,
+    normalised (lengths in mm, material constants centred on their ranges)."""
+    tip, yaw = trajectory_state(scene.keyframes, k)
+    tip0, yaw0 = trajectory_state(scene.keyframes, 0)
+    L = scene.gel.cx * scene.gel.dx
+    press = max(0.0, scene.gel.height - tip[2])
+    m = scene.mat
+    return np.array([press / MM, (tip[0] - tip0[0]) / MM, (tip[1] - tip0[1]) / MM, yaw - yaw0,
+                     (m.E - 1.9e5) / 1e5, (m.nu - 0.44) / 0.04, (scene.ind.mu - 0.6) / 0.4,
+                     (tip[0] - L / 2) / MM, (tip[1] - L / 2) / MM], np.float32)
+
+
+@dataclasses.dataclass
+class Frames:
+    """A frame dataset on the device."""
+    height: "object"          # [N, P, P] float32, indenter heightmap (mm)
+    scalars: "object"         # [N, 9] float32
+    disp: "object"            # [N, P, P, 3] float32, surface displacement (mm)
+    press: np.ndarray         # [N] trajectory press depth (mm)
+    traj: np.ndarray          # [N] trajectory index
+    substep: np.ndarray       # [N]
+    mpm_seconds: float = 0.0  # device time of the IMPM stepping that made them
+    mpm_frames: int = 0
+
+    def __len__(self):
+        return int(self.press.shape[0])
+
+    def subset(self, idx):
+        idx = np.asarray(idx)
+        torch = _torch()
+        ti = torch.as_tensor(idx, device=self.height.device)
+        return Frames(self.height[ti], self.scalars[ti], self.disp[ti], self.press[idx], self.traj[idx],
+                      self.substep[idx], self.mpm_seconds, self.mpm_frames)
+
+
+def _run_chunk(chunk, every, px, pitch, x_ref):
+    """IMPM of one batch of trajectories; returns (H, U, seconds, passes per instance-substep)."""
+    torch = _torch()
+    nf = chunk[0].n_substeps // every
+    H = torch.empty((len(chunk), nf, px, px), dtype=torch.float32, device="cuda")
+    U = torch.empty((len(chunk), nf, px, px, 3), dtype=torch.float32, device="cuda")
+    sim = T.Sim(chunk, use_graph=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    secs = 0.0
+    try:
+        for f in range(nf):
+            ev0.record()
+            sim.step(every)
+            ev1.record()
+            ev1.synchronize()
+            secs += ev0.elapsed_time(ev1) / 1e3
+            for i in range(len(chunk)):
+                T.tsim_read_indenter_height(sim.ctx, i, px, px, pitch, CLIP, out=H[i, f])
+                T.tsim_read_displacement(sim.ctx, i, x_ref, px, px, pitch, out=U[i, f])
+        st = T.tsim_stats(sim.ctx)
+    finally:
+        sim.close()
+    return H, U, secs, st.passes / max(1, st.substeps) / len(chunk)
+
+
+def generate(scenes, every: int = 100, batch: int = 64, log=None, retries: int = 3) -> Frames:
+    """IMPM frames of ``scenes`` (all on the same pad), ``batch`` trajectories
+    per context.  A trajectory whose simulation latches an error (the message
+    names its instance) is left out and the rest of its batch is run again."""
+    torch = _torch()
+    px = scenes[0].readout_px
+    pitch = scenes[0].readout_pitch
+    gel = scenes[0].gel
+    x_ref = torch.from_numpy(np.ascontiguousarray(I.gel_particles(gel)[0])).cuda()
+    hs, ss, us, pr, tr, sk = [], [], [], [], [], []
+    mpm_s, mpm_frames, dropped = 0.0, 0, []
+    for c0 in range(0, len(scenes), batch):
+        ids = list(range(c0, min(len(scenes), c0 + batch)))
+        nsub = scenes[ids[0]].n_substeps
+        assert all(scenes[j].n_substeps == nsub and scenes[j].gel == gel for j in ids)
+        nf = nsub // every
+        for attempt in range(retries + 1):
+            try:
+                H, U, secs, passes = _run_chunk([scenes[j] for j in ids], every, px, pitch, x_ref)
+                break
+            except T.TsimError as e:
+                m = re.search(r"instance (\d+)", str(e))
+                if m is None or attempt == retries:
+                    raise
+                bad = ids.pop(int(m.group(1)))
+                dropped.append(bad)
+                if log:
+                    log("trajectory %d left out: %s" % (bad, e))
+        mpm_s += secs
+        mpm_frames += nf * len(ids)
+        for i, j in enumerate(ids):
+            for f in range(nf):
+                k = (f + 1) * every
+                ss.append(frame_scalars(scenes[j], k))
+                pr.append(scenes[j].meta.get("press", 0.0) / MM)
+                tr.append(j)
+                sk.append(k)
+        hs.append((H / MM).reshape(-1, px, px))
+        us.append((U / MM).reshape(-1, px, px, 3))
+        if log:
+            log("generated %d/%d trajectories, %.1f s of IMPM, %.2f passes per instance-substep"
+                % (ids[-1] + 1, len(scenes), mpm_s, passes))
+    out = Frames(torch.cat(hs), torch.from_numpy(np.stack(ss)).cuda(), torch.cat(us), np.array(pr, np.float64),
+                 np.array(tr), np.array(sk), mpm_s, mpm_frames)
+    out.dropped = dropped
+    return out
+
+
+def features(fr: Frames, idx=None):
+    """Network input x[B, P, P, 12] for frames ``idx`` (all when None)."""
+    torch = _torch()
+    h = fr.height if idx is None else fr.height[idx]
+    sc = fr.scalars if idx is None else fr.scalars[idx]
+    B, P, _ = h.shape
+    lin = (torch.arange(P, device=h.device, dtype=torch.float32) + 0.5) / P * 2 - 1
+    x = torch.empty((B, P, P, 12), dtype=torch.float32, device=h.device)
+    x[..., 0] = h
+    x[..., 1] = lin.view(1, 1, P)
+    x[..., 2] = lin.view(1, P, 1)
+    x[..., 3:] = sc.view(B, 1, 1, N_SCALARS)
+    return x
+
+
+def train(fr: Frames, steps: int, batch: int = 32, lr: float = 1e-3, seed: int = 0, params=None, log=None,
+          log_every: int = 1000, weight: str = "press", warmup: int = 200):
+    """Train from ``params`` (seeded init when None); returns (params, losses).
+
+    ``weight="press"`` weights each frame by 1/press_depth^2 (through the
+    loss mask, normalised to mean 1 over the dataset) so that the loss
+    follows the error measure, which is relative to the press depth."""
+    torch = _torch()
+    P = fr.height.shape[1]
+    net = S.tsurr_create(batch, P, P)
+    try:
+        S.tsurr_set_params(net, S.init_params(seed) if params is None else params)
+        if weight == "press":
+            w = 1.0 / np.maximum(fr.press, 0.05) ** 2
+            w = torch.as_tensor(w / w.mean(), dtype=torch.float32, device="cuda")
+        else:
+            w = torch.ones(len(fr), dtype=torch.float32, device="cuda")
+        rng = np.random.default_rng(seed)
+        losses = []
+        t0 = time.time()
+        for step in range(1, steps + 1):
+            idx = torch.as_tensor(rng.integers(0, len(fr), batch), device="cuda")
+            x = features(fr, idx)
+            t = fr.disp[idx].contiguous()
+            m = w[idx].view(batch, 1, 1).expand(batch, P, P).contiguous()
+            losses.append(S.tsurr_backward(net, x, t, m))
+            # linear warm-up, then cosine decay to 2 % of the peak rate
+            c = 0.02 + 0.98 * 0.5 * (1 + math.cos(math.pi * (step - 1) / steps))
+            lr_t = lr * min(1.0, step / max(1, warmup)) * c
+            S.tsurr_adam(net, lr_t, 0.9, 0.999, 1e-8, step)
+            if log and (step % log_every == 0 or step == steps):
+                log("step %d loss %.5f (%.1f s)" % (step, float(np.mean(losses[-log_every:])), time.time() - t0))
+        return S.tsurr_get_params(net), np.array(losses)
+    finally:
+        S.tsurr_destroy(net)
+
+
+def predict(params, fr: Frames, batch: int = 256):
+    """Network output y[N, P, P, 4] (mm) for all frames."""
+    torch = _torch()
+    P = fr.height.shape[1]
+    net = S.tsurr_create(batch, P, P)
+    try:
+        S.tsurr_set_params(net, params)
+        y = torch.empty((len(fr), P, P, 4), dtype=torch.float32, device="cuda")
+        for a in range(0, len(fr), batch):
+            idx = torch.arange(a, min(len(fr), a + batch), device="cuda")
+            S.tsurr_forward(net, features(fr, idx), out=y[a:a + idx.numel()])
+        torch.cuda.synchronize()
+        return y
+    finally:
+        S.tsurr_destroy(net)
+
+
+def frame_errors(pred, fr: Frames):
+    """Per-frame RMS over the pixels of |u_pred - u_IMPM|, divided by the
+    trajectory's press depth."""
+    torch = _torch()
+    d = pred[..., :3] - fr.disp
+    rms = torch.sqrt((d * d).sum(-1).mean(dim=(1, 2))).cpu().numpy()
+    return rms / fr.press
+
+
+def indicator(pred, fr: Frames):
+    """Predicted per-frame RMS error (indicator channel), divided by press depth."""
+    torch = _torch()
+    e = pred[..., 3]
+    return torch.sqrt((e * e).mean(dim=(1, 2))).cpu().numpy() / fr.press
+
+
+def foil(fr: Frames, sigma_px: float):
+    """No-learning prediction: u_z = -(Gaussian-smoothed indenter penetration)."""
+    torch = _torch()
+    pen = torch.clamp(-fr.height, min=0.0).unsqueeze(1)
+    r = max(1, int(math.ceil(3 * sigma_px)))
+    g = torch.exp(-0.5 * (torch.arange(-r, r + 1, device="cuda", dtype=torch.float32) / sigma_px) ** 2)
+    g = g / g.sum()
+    import torch.nn.functional as F
+    sm = F.conv2d(F.pad(pen, (r, r, 0, 0), mode="replicate"), g.view(1, 1, 1, -1))
+    sm = F.conv2d(F.pad(sm, (0, 0, r, r), mode="replicate"), g.view(1, 1, -1, 1))
+    out = torch.zeros((len(fr),) + tuple(fr.height.shape[1:]) + (4,), device="cuda")
+    out[..., 2] = -sm[:, 0]
+    return out
+
+
+def fit_foil(fr: Frames, sigmas=(0.5, 1, 2, 3, 4, 6, 8, 12)):
+    """The foil's one parameter, chosen by its error on ``fr``."""
+    best = None
+    for s in sigmas:
+        e = float(np.median(frame_errors(foil(fr, s), fr)))
+        if best is None or e < best[1]:
+            best = (s, e)
+    return best[0]
+
+
+def serve_summary(err, ind, threshold: float = 0.02):
+    """Fallback rule and the error of what is served: frames whose indicator
+    exceeds ``threshold`` go to the simulator (served error 0)."""
+    fb = ind > threshold
+    served = np.where(fb, 0.0, err)
+    return dict(n=int(err.size), fallback_frac=float(fb.mean()), served_within=float((served <= threshold).mean()),
+                surrogate_within=float((err <= threshold).mean()), median_err=float(np.median(err)),
+                p90_err=float(np.percentile(err, 90)), max_served_err=float(served.max()))
+
+
+def time_inference(params, P: int = 128, batch: int = 256, reps: int = 20, warmup: int = 3, seed: int = 0):
+    """Seconds per batch of the network forward on device-resident inputs
+    (CUDA events on the launching stream)."""
+    torch = _torch()
+    net = S.tsurr_create(batch, P, P)
+    try:
+        S.tsurr_set_params(net, params)
+        x = torch.from_numpy(I.surrogate_batch(seed, batch, P, P)[0]).cuda()
+        y = torch.empty((batch, P, P, 4), dtype=torch.float32, device="cuda")
+        for _ in range(warmup):
+            S.tsurr_forward(net, x, out=y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            S.tsurr_forward(net, x, out=y)
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+    finally:
+        S.tsurr_destroy(net)
+
+
+def forward_flops(P: int = 128) -> float:
+    """Multiply-add FLOPs of one P x P frame through the nine convolutions
+    (2 per multiply-add, the 16-wide stored input and output included)."""
+    tot, hw = 0.0, P * P
+    sizes = [hw, hw / 4, hw / 16, hw / 64, hw / 64, hw / 16, hw / 4, hw, hw]
+    for (cin, cout), npix in zip(I.SURR_CONVS, sizes):
+        tot += 2.0 * npix * cout * 9 * cin
+    return tot
+
+
+def save(path, params, meta: dict):
+    np.savez_compressed(path, params=np.asarray(params, np.float32), meta=json.dumps(meta))
+
+
+def load_params(path):
+    z = np.load(path, allow_pickle=False)
+    return z["params"], json.loads(str(z["meta"]))

@@ -17,7 +17,7 @@ TSURR_CIN = 12
 TSURR_COUT = 4
 
 EXPORTS = ["tsurr_create", "tsurr_num_params", "tsurr_set_params", "tsurr_get_params", "tsurr_get_grads",
-           "tsurr_forward", "tsurr_backward", "tsurr_adam", "tsurr_destroy"]
+           "tsurr_forward", "tsurr_backward", "tsurr_adam", "tsurr_sync", "tsurr_destroy"]
 
 # (cin, cout, stride, upsample, relu, skip source layer or -1) per layer; the
 # network input is padded from 12 to 16 channels, the output stored as 16.
@@ -42,6 +42,7 @@ def load():
             "tsurr_forward": (C.c_int, [vp, vp, C.c_int, vp, C.c_int]),
             "tsurr_backward": (C.c_int, [vp, vp, vp, vp, C.c_int, P(C.c_double), C.c_int]),
             "tsurr_adam": (C.c_int, [vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int]),
+            "tsurr_sync": (C.c_int, [vp]),
             "tsurr_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -130,6 +131,10 @@ def tsurr_backward(net, x, target, mask) -> float:
 
 def tsurr_adam(net, lr, beta1=0.9, beta2=0.999, eps=1e-8, t=1):
     _t._check(load().tsurr_adam(net, float(lr), float(beta1), float(beta2), float(eps), int(t)))
+
+
+def tsurr_sync(net):
+    _t._check(load().tsurr_sync(net))
 
 
 def tsurr_destroy(net):
