@@ -91,8 +91,9 @@ struct Conv {
 // mbarrier; the epilogue reads D back with tcgen05.ld (warp w owns TMEM lanes
 // 32w..32w+31, i.e. its 32 pixels) and fuses bias, skip and ReLU.
 constexpr int TC_M = 128;          // output pixels per CTA (UMMA M)
-constexpr int TC_STAGES = 4;       // shared-memory stages of 64 K each (4 UMMAs of K = 16)
-constexpr int TC_DIST = 2;         // k-tiles loaded ahead of the one being multiplied
+constexpr int TC_MAX_STAGES = 16;  // shared-memory stages of 64 K each (4 UMMAs of K = 16); k-tiles are
+                                   // loaded stages - 2 ahead, so a stage is refilled only after the
+                                   // UMMAs that read it two iterations ago have completed
 constexpr uint32_t TC_LBO = 128;   // bytes between the two K halves (core matrices) of a K16 slice
 constexpr uint32_t TC_SBO = 256;   // bytes between 8-row groups of a K16 slice
 constexpr int TC_WAIT = 1 << 22;   // polls before a wait gives up
@@ -103,7 +104,6 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait()
 {
@@ -113,10 +113,6 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void bar_init(uint32_t bar)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-}
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity)
 {
     for (int it = 0; it < TC_WAIT; ++it) {
@@ -172,146 +168,227 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// dynamic shared memory of k_conv_fwd_tc for cout channels
+// dynamic shared memory of k_conv_fwd_tc for cout channels: as many stages
+// as fit in 220 KB (3 .. 16)
+constexpr uint32_t TC_SMEM_MAX = 220u * 1024u;
 __host__ __device__ inline uint32_t tc_stage_bytes(int cout) { return 4u * (TC_M * 32u + (uint32_t)cout * 32u); }
-__host__ __device__ inline uint32_t tc_smem_bytes(int cout) { return TC_STAGES * tc_stage_bytes(cout) + 1024 + 64; }
+__host__ __device__ inline int tc_stages(int cout)
+{
+    const int s = (int)((TC_SMEM_MAX - 2048u) / tc_stage_bytes(cout));
+    return s < 3 ? 3 : (s > TC_MAX_STAGES ? TC_MAX_STAGES : s);
+}
+__host__ __device__ inline uint32_t tc_smem_bytes(int cout)
+{
+    return (uint32_t)tc_stages(cout) * tc_stage_bytes(cout) + 1024 + 16 * TC_MAX_STAGES + 64;
+}
 
-__global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(Conv c, int *err)
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void bar_init_n(uint32_t bar, uint32_t n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(n) : "memory");
+}
+
+constexpr int TC_THREADS = 288;    // warps 0-3 load, warps 4-7 run the epilogue, warp 8 issues the UMMAs
+
+__device__ __forceinline__ void bar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// TMEM columns for two accumulators of n columns (a power of two >= 32)
+__host__ __device__ inline uint32_t tc_tmem_cols(int n)
+{
+    uint32_t c = 32;
+    while (c < 2u * (uint32_t)n) c <<= 1;
+    return c;
+}
+
+// Persistent, warp-specialised: each CTA walks output tiles of 128 pixels
+// (tile = blockIdx.x, += gridDim.x).  The loaders fill a ring of stages of
+// 64 K with cp.async and signal full[s] when their copies land
+// (cp.async.mbarrier.arrive.noinc, 128 arrivals); the issuing thread waits on
+// full[s], fences the generic-proxy writes against the tensor core's
+// async-proxy reads, issues the stage's UMMAs into accumulator (tile & 1) and
+// commits them to empty[s]; at the end of a tile it commits to accf[b].  The
+// epilogue warps drain accumulator b with tcgen05.ld while the next tile
+// accumulates into the other one, then release it on acce[b].  The issuing
+// warp never has copies in flight, so its proxy fence does not wait for the
+// loads of later stages.
+__global__ void __launch_bounds__(TC_THREADS, 1) k_conv_fwd_tc(Conv c, int *err)
 {
     extern __shared__ unsigned char tc_raw[];
     const int N = c.cout, K = 9 * c.cin, M = c.B * c.hout * c.wout;
-    const int nk16 = K / 16, nkt = (nk16 + 3) / 4;
+    const int nk16 = K / 16, nkt = (nk16 + 3) / 4, ntiles = (M + TC_M - 1) / TC_M;
     const uint32_t a_bytes = TC_M * 32, b_bytes = (uint32_t)N * 32, stage_bytes = tc_stage_bytes(N);
-    // stages 1024-byte aligned; barriers and the TMEM address after them
+    const int NS = tc_stages(N);
+    // stages 1024-byte aligned; then full[16], empty[16], accf[2], acce[2], the TMEM address
     const uint32_t raw = saddr(tc_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *stages = tc_raw + (base - raw);
-    const uint32_t bars = base + TC_STAGES * stage_bytes;           // TC_STAGES x 8 bytes
-    const uint32_t tslot = bars + 8 * TC_STAGES;
-    uint32_t *tslot_p = reinterpret_cast<uint32_t *>(stages + TC_STAGES * stage_bytes + 8 * TC_STAGES);
+    const uint32_t full = base + NS * stage_bytes, empty = full + 8 * TC_MAX_STAGES;
+    const uint32_t accf = empty + 8 * TC_MAX_STAGES, acce = accf + 16, tslot = acce + 16;
+    const uint32_t *tslot_p = reinterpret_cast<const uint32_t *>(stages + (tslot - base));
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int m0 = blockIdx.x * TC_M;
-    const uint32_t ncols = N < 32 ? 32u : (uint32_t)N;
+    const uint32_t ncols = tc_tmem_cols(N);
 
-    if (warp == 0) {
+    if (warp == 8) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (t == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) bar_init(bars + 8 * s);
+        for (int s = 0; s < NS; ++s) {
+            bar_init_n(full + 8 * s, 128);
+            bar_init_n(empty + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init_n(accf + 8 * b, 1);
+            bar_init_n(acce + 8 * b, 128);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot_p;
-
-    // loader: thread t moves 16-byte chunk q = t & 7 of rows (t >> 3) + 16 i;
-    // chunk q is K half (q & 1) of K16 slice (q >> 1) of the stage
-    const int q = t & 7, slice = q >> 1, half = q & 1, r0 = t >> 3;
-    int rb[8], ry[8], rx[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int m = m0 + r0 + 16 * i;
-        if (m < M) {
-            rx[i] = m % c.wout;
-            ry[i] = (m / c.wout) % c.hout;
-            rb[i] = m / (c.wout * c.hout);
-        } else {
-            rb[i] = -1;
-            ry[i] = rx[i] = 0;
-        }
-    }
-    auto load_tile = [&](int kt, int s) {
-        const int k16 = kt * 4 + slice;
-        if (k16 >= nk16) return;
-        const int k = k16 * 16 + half * 8;
-        const int kk = k / c.cin, ci = k % c.cin, ky = kk / 3, kx = kk % 3;
-        const uint32_t sa = saddr(stages + s * stage_bytes) + slice * a_bytes + half * 128;
-        const uint32_t sb = saddr(stages + s * stage_bytes) + 4 * a_bytes + slice * b_bytes + half * 128;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int r = r0 + 16 * i;
-            int iy = ry[i] * c.stride + ky - 1, ix = rx[i] * c.stride + kx - 1;
-            const bool v = rb[i] >= 0 && iy >= 0 && iy < c.hl && ix >= 0 && ix < c.wl;
-            if (c.up) { iy >>= 1; ix >>= 1; }
-            const bf16 *src = v ? c.in + (((size_t)rb[i] * c.hin + iy) * c.win + ix) * c.cin + ci : c.in;
-            cp_async16(sa + (r >> 3) * TC_SBO + (r & 7) * 16, src, v ? 16u : 0u);
-        }
-        for (int n = r0; n < N; n += 16)
-            cp_async16(sb + (n >> 3) * TC_SBO + (n & 7) * 16, c.w + (size_t)n * K + k, 16u);
-    };
-
-    const uint32_t idesc = umma_idesc(TC_M, N);
     bool ok = true;
-    for (int j = 0; j < TC_DIST; ++j) {
-        if (j < nkt) load_tile(j, j);
-        cp_async_commit();
-    }
-    for (int kt = 0; kt < nkt; ++kt) {
-        const int nx = kt + TC_DIST;
-        if (nx < nkt) {
-            const int s = nx % TC_STAGES;
-            // the stage was last read by the UMMAs of k-tile nx - TC_STAGES
-            if (nx >= TC_STAGES && ok) ok = bar_wait(bars + 8 * s, ((nx - TC_STAGES) / TC_STAGES) & 1);
-            if (ok) load_tile(nx, s);
+
+    if (warp < 4) {
+        // loader: thread t moves 16-byte chunk q = t & 7 of rows (t >> 3) + 16 i;
+        // chunk q is K half (q & 1) of K16 slice (q >> 1) of the stage
+        const int q = t & 7, slice = q >> 1, half = q & 1, r0 = t >> 3;
+        uint32_t g = 0;                                // k-tiles loaded so far (ring position)
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            int rb[8], ry[8], rx[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int m = tile * TC_M + r0 + 16 * i;
+                if (m < M) {
+                    rx[i] = m % c.wout;
+                    ry[i] = (m / c.wout) % c.hout;
+                    rb[i] = m / (c.wout * c.hout);
+                } else {
+                    rb[i] = -1;
+                    ry[i] = rx[i] = 0;
+                }
+            }
+            for (int kt = 0; kt < nkt; ++kt, ++g) {
+                const uint32_t s = g % NS;
+                // the stage was last read by the UMMAs of ring position g - NS
+                if (g >= (uint32_t)NS && !bar_wait(empty + 8 * s, ((g / NS) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                const int k16 = kt * 4 + slice;
+                if (k16 < nk16) {
+                    const int k = k16 * 16 + half * 8;
+                    const int kk = k / c.cin, ci = k % c.cin, ky = kk / 3, kx = kk % 3;
+                    const uint32_t sa = base + s * stage_bytes + slice * a_bytes + half * 128;
+                    const uint32_t sb = base + s * stage_bytes + 4 * a_bytes + slice * b_bytes + half * 128;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int r = r0 + 16 * i;
+                        int iy = ry[i] * c.stride + ky - 1, ix = rx[i] * c.stride + kx - 1;
+                        const bool v = rb[i] >= 0 && iy >= 0 && iy < c.hl && ix >= 0 && ix < c.wl;
+                        if (c.up) { iy >>= 1; ix >>= 1; }
+                        const bf16 *src =
+                            v ? c.in + (((size_t)rb[i] * c.hin + iy) * c.win + ix) * c.cin + ci : c.in;
+                        cp_async16(sa + (r >> 3) * TC_SBO + (r & 7) * 16, src, v ? 16u : 0u);
+                    }
+                    for (int n = r0; n < N; n += 16)
+                        cp_async16(sb + (n >> 3) * TC_SBO + (n & 7) * 16, c.w + (size_t)n * K + k, 16u);
+                }
+                cp_async_arrive(full + 8 * s);
+            }
         }
-        cp_async_commit();
-        cp_async_wait<TC_DIST>();
-        fence_proxy_async();
-        ok = __syncthreads_and(ok);
-        if (t == 0 && ok) {
+        cp_async_wait<0>();
+    } else if (warp == 8) {
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc(TC_M, N);
+            uint32_t g = 0;
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+                const int b = it & 1;
+                // accumulator b was last drained by the epilogue of tile it - 2
+                if (it >= 2 && !bar_wait(acce + 8 * b, ((it >> 1) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * N);
+                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                    const uint32_t s = g % NS;
+                    if (!bar_wait(full + 8 * s, (g / NS) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_proxy_async();
+                    tc_fence_after();
+                    const uint32_t sa = base + s * stage_bytes, sb = sa + 4 * a_bytes;
+                    for (int j = 0; j < 4 && kt * 4 + j < nk16; ++j)
+                        umma_bf16(d, umma_desc(sa + j * a_bytes), umma_desc(sb + j * b_bytes), idesc,
+                                  (kt | j) != 0);
+                    umma_commit(empty + 8 * s);
+                }
+                umma_commit(accf + 8 * b);      // tracks every UMMA of the tile
+            }
+        }
+    } else {
+        // epilogue: warp 4 + e reads TMEM lanes 32e .. 32e + 31 = pixels 32e .. 32e + 31 of the tile
+        const int e = warp - 4;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+            const int b = it & 1;
+            // warp-uniform decision: tcgen05.ld below must be executed by all 32 lanes
+            if (!__all_sync(0xffffffffu, bar_wait(accf + 8 * b, (it >> 1) & 1))) {
+                ok = false;
+                break;
+            }
             tc_fence_after();
-            const int s = kt % TC_STAGES;
-            const uint32_t sa = saddr(stages + s * stage_bytes), sb = sa + 4 * a_bytes;
-            for (int j = 0; j < 4 && kt * 4 + j < nk16; ++j)
-                umma_bf16(tmem, umma_desc(sa + j * a_bytes), umma_desc(sb + j * b_bytes), idesc, (kt | j) != 0);
-            umma_commit(bars + 8 * s);
-        }
-    }
-    if (ok) ok = bar_wait(bars + 8 * ((nkt - 1) % TC_STAGES), ((nkt - 1) / TC_STAGES) & 1);
-    cp_async_wait<0>();
-    ok = __syncthreads_and(ok);
-    tc_fence_after();
-    if (ok) {
-        const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < N; c0 += 16) {
-            uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            if (row >= M) continue;
-            float v[16];
+            const int row = tile * TC_M + e * 32 + lane;
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(b * N + c0), r);
+                if (row >= M) continue;
+                float v[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) + c.bias[c0 + j];
-            if (c.skip) {
-                const uint4 *sp = reinterpret_cast<const uint4 *>(c.skip + (size_t)row * N + c0);
-                uint4 s2[2] = {sp[0], sp[1]};
-                const bf16 *se = reinterpret_cast<const bf16 *>(s2);
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) + c.bias[c0 + j];
+                if (c.skip) {
+                    const uint4 *sp = reinterpret_cast<const uint4 *>(c.skip + (size_t)row * N + c0);
+                    uint4 s2[2] = {sp[0], sp[1]};
+                    const bf16 *se = reinterpret_cast<const bf16 *>(s2);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] += bf2f(se[j]);
+                    for (int j = 0; j < 16; ++j) v[j] += bf2f(se[j]);
+                }
+                if (c.relu) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
+                }
+                if (c.out32) {
+                    for (int j = 0; j < 16 && c0 + j < c.out32_ch; ++j)
+                        c.out32[(size_t)row * c.out32_ch + c0 + j] = v[j];
+                } else {
+                    uint4 o2[2];
+                    bf16 *oe = reinterpret_cast<bf16 *>(o2);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) oe[j] = f2bf(v[j]);
+                    uint4 *op = reinterpret_cast<uint4 *>(c.out + (size_t)row * N + c0);
+                    op[0] = o2[0];
+                    op[1] = o2[1];
+                }
             }
-            if (c.relu) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
-            }
-            if (c.out32) {
-                for (int j = 0; j < 16 && c0 + j < c.out32_ch; ++j) c.out32[(size_t)row * c.out32_ch + c0 + j] = v[j];
-            } else {
-                uint4 o2[2];
-                bf16 *oe = reinterpret_cast<bf16 *>(o2);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) oe[j] = f2bf(v[j]);
-                uint4 *op = reinterpret_cast<uint4 *>(c.out + (size_t)row * N + c0);
-                op[0] = o2[0];
-                op[1] = o2[1];
-            }
+            tc_fence_before();
+            bar_arrive(acce + 8 * b);
         }
     }
     tc_fence_before();
-    __syncthreads();
-    if (warp == 0)
+    const bool all_ok = __syncthreads_and(ok);
+    if (warp == 8)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
-    if (t == 0 && !ok) atomicOr(err, 1);
+    if (t == 0 && !all_ok) atomicOr(err, 1);
 }
 
 // ---------------------------------------------------------------- data gradient
@@ -572,6 +649,7 @@ struct tsurr_net {
     double *loss = nullptr;
     float *xbuf = nullptr, *tbuf = nullptr, *mbuf = nullptr;
     int *err = nullptr;          // set by a kernel whose bounded wait gave up
+    int num_sms = 1;
     std::vector<void *> allocs;
 };
 
@@ -706,7 +784,11 @@ extern "C" int tsurr_create(int max_batch, int height, int width, void *stream, 
     cudaMemsetAsync(n->m2, 0, n->nparam * 4, n->s);
     cudaMemsetAsync(n->wmem, 0, wtotal * 2 * sizeof(bf16), n->s);
     cudaMemsetAsync(n->err, 0, 64, n->s);
-    if (cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(256)) !=
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n->num_sms < 1)
+        n->num_sms = 1;
+    if (cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(TC_SMEM_MAX + 2048)) !=
             cudaSuccess ||
         cudaStreamSynchronize(n->s) != cudaSuccess) {
         for (void *p : n->allocs) cudaFree(p);
@@ -776,8 +858,9 @@ static int run_forward(tsurr_net *n, const float *x, int B)
             c.out32 = n->y;
             c.out32_ch = TSURR_COUT;
         }
-        const unsigned grid = cdiv((long long)B * c.hout * c.wout, TC_M);
-        k_conv_fwd_tc<<<grid, 128, tc_smem_bytes(c.cout), n->s>>>(c, n->err);
+        const long long tiles = cdiv((long long)B * c.hout * c.wout, TC_M);
+        const unsigned grid = (unsigned)std::min<long long>(tiles, n->num_sms);    // one CTA per SM
+        k_conv_fwd_tc<<<grid, TC_THREADS, tc_smem_bytes(c.cout), n->s>>>(c, n->err);
     }
     SCU(cudaGetLastError());
     return TSIM_OK;
