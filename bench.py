@@ -210,7 +210,7 @@ def surrogate_leg(n_traj=8, threshold=0.02):
             "inference_batch": 256, "frame": "128x128x3 displacement + indicator",
             "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                          "frac": tflops / peak, "peak_source": src,
-                         "kernel": "k_conv_fwd (mma.sync m16n8k16 BF16, FP32 accumulate), whole forward"},
+                         "kernel": "k_conv_fwd_tc (tcgen05.mma kind::f16, BF16 in, FP32 accumulate in TMEM), whole forward"},
             "weights": os.path.relpath(SURROGATE_WEIGHTS, ROOT), "trained": meta}
 
 

@@ -102,7 +102,7 @@ __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cv
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t bytes)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 template <int N>
 __device__ __forceinline__ void cp_async_wait()
