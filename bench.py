@@ -240,6 +240,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="pad4m", choices=["pad4m", "press65k", "batch64", "large33m"])
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate vs IMPM frames/s leg")
+    ap.add_argument("--autotune", type=int, default=600,
+                    help="substeps of online launch-configuration tuning before the timed region (0: off)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch kernels one by one (profilers cannot see inside graphs with loops)")
     args = ap.parse_args()
@@ -302,6 +304,9 @@ def main():
     reset()
     for _ in range(args.warmup):
         one_step()
+    tuning = T.tsim_get_tuning(ctx)
+    if args.autotune > 0:
+        tuning = T.tsim_autotune(ctx, args.autotune)
     reset()
     T.tsim_kernel_time(ctx)                    # drop warm-up timings
     s0 = T.tsim_stats(ctx)
@@ -382,7 +387,8 @@ def main():
                    "particle_substeps_per_s": n * substeps * world / (t_max * 1e-3),
                    "substep_ms": t_max / max(substeps, 1),
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (particle state %d MB per parity)" % (n * 52 // 2 ** 20)},
+                   "l2": "inputs larger than L2 (particle state %d MB per parity)" % (n * 52 // 2 ** 20),
+                   "tuning": tuning},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _traffic(n),
                      "kernel": "k_transfer<COMMIT> (fused G2P -> F,x move -> re-bin -> P2G)",

@@ -232,6 +232,36 @@ int tsim_sync(tsim_ctx *ctx);
 /* Counters; synchronises. */
 int tsim_stats(tsim_ctx *ctx, tsim_stats_t *out);
 
+/* Execution configuration of the substep schedule.  It changes how the same
+ * kernels are launched, never what they compute, so the state evolves as
+ * under any other configuration.  Batched contexts of uneven instances are
+ * where the choice matters (project addition: the paper has no counterpart). */
+typedef struct {
+    int grid_threads;      /* threads per CTA of the grid update: 128, 256 or 512 */
+    int grid_flat;         /* 0: one launch row per instance, sized by the largest
+                              instance; 1: one 1-D launch over the node ranges of
+                              all instances packed back to back */
+    int graph_chunk;       /* substeps per CUDA graph launch in graph mode (1..200) */
+    float us_per_mupdate;  /* set by tsim_autotune: measured microseconds per
+                              million particle-updates of the chosen configuration */
+} tsim_tuning_t;
+
+/* Set (synchronises; rebuilds graphs) or read the configuration.  Default:
+ * 256 threads, per-instance rows, 20 substeps per graph. */
+int tsim_set_tuning(tsim_ctx *ctx, const tsim_tuning_t *cfg);
+int tsim_get_tuning(tsim_ctx *ctx, tsim_tuning_t *out);
+
+/* Autotuner: advance by n substeps as tsim_step(n) would, timing the
+ * candidate configurations on successive equal windows of those substeps
+ * (CUDA events; cost per particle-update): the six grid-update shapes
+ * {128, 256, 512 threads} x {per-instance, packed} in two interleaved
+ * rounds, then in graph mode the chunk lengths {10, 20, 40} with the best
+ * shape.  The fastest is kept for later calls and written to *out (may be
+ * NULL).  n must allow windows of >= 2 substeps (stream mode; n >= 24) or of
+ * a multiple of 40 (graph mode; n >= 600), else TSIM_ERR_INVALID_ARG.
+ * Synchronises after every window; latched device errors are returned. */
+int tsim_autotune(tsim_ctx *ctx, int n_substeps, tsim_tuning_t *out);
+
 /* Capture the substep sequence in a CUDA graph with a device-driven loop
  * over relative-rest passes (enable != 0) or launch kernels one by one. */
 int tsim_use_graph(tsim_ctx *ctx, int enable);

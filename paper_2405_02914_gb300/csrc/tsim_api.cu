@@ -58,8 +58,12 @@ struct tsim_ctx {
     float *pick = nullptr;              // marker positions (4096*3)
     // graph execution
     bool use_graph = false;
-    std::vector<GraphChunk> chunks;     // ring of graph executables of `chunk` substeps
-    int chunk = 0, chunk_next = 0;
+    std::vector<GraphChunk> chunks;     // ring of graph executables of chunk_len substeps
+    int chunk_next = 0;
+    // execution configuration (tsim_set_tuning / tsim_autotune); no effect on results
+    int chunk_len = 20;
+    int grid_threads = 256, grid_flat = 0;
+    float tuned_us = 0.f;
     // profiling of the commit transfer
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -81,7 +85,7 @@ static void free_all(tsim_ctx *c)
     Dev &d = c->d;
     void *ptrs[] = {d.P[0], d.P[1], d.T[0], d.T[1], d.cnt[0], d.cnt[1], d.VC, d.acc, d.vel,
                     d.blk_inst, d.inst, d.ist, d.G, (void *)d.kf, (void *)d.perm, d.log,
-                    d.sx, d.sv, d.sC, d.sF, d.stag, c->ro, c->ids, c->pick};
+                    d.sx, d.sv, d.sC, d.sF, d.stag, c->ro, c->ids, c->pick, (void *)d.gchunk};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &g : c->chunks) {
@@ -190,6 +194,14 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
     c->total_nodes = nodes;
     c->total_particles = parts;
     Dev &d = c->d;
+    // packed grid-update launch table: 128-node chunks, instances padded to 512 nodes
+    std::vector<int2> gch;
+    for (int i = 0; i < n_inst; ++i) {
+        const long long nn = (long long)c->hinst[i].nx * c->hinst[i].ny * c->hinst[i].nz;
+        const long long nch = (nn + 511) / 512 * 4, first = (long long)gch.size();
+        for (long long a = 0; a < nch; ++a) gch.push_back(make_int2(i, (int)first));
+    }
+    d.n_gchunk = (long long)gch.size();
     d.S = blocks * CAP;
     d.n_inst = n_inst;
     const size_t S = (size_t)d.S;
@@ -210,6 +222,7 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
         {(void **)&d.sC, parts * 9 * sizeof(float)},      {(void **)&d.sF, parts * 9 * sizeof(float)},
         {(void **)&d.stag, parts * sizeof(uint32_t)},     {(void **)&c->ro, (size_t)RO_MAX * 6 * sizeof(float)},
         {(void **)&c->ids, MARK_MAX * sizeof(int)},       {(void **)&c->pick, MARK_MAX * 3 * sizeof(float)},
+        {(void **)&d.gchunk, gch.size() * sizeof(int2)},
     };
     for (auto &a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.bytes);
@@ -238,6 +251,8 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
     chk(cudaMemsetAsync(d.log, 0, n_inst * LOGN * sizeof(int2), c->stream));
     chk(cudaMemsetAsync(d.VC, 0, S * 12 * sizeof(float), c->stream));
     chk(cudaMemcpyAsync(d.blk_inst, bi.data(), blocks * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    chk(cudaMemcpyAsync((void *)d.gchunk, gch.data(), gch.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                        c->stream));
     std::vector<int> perm(n_inst * 256);
     for (int i = 0; i < n_inst; ++i)
         for (int a = 0; a < 256; ++a) perm[i * 256 + a] = a;
@@ -442,11 +457,11 @@ static int launch_substeps_stream(tsim_ctx *c, int n)
     const int limit = c->solver.relrest_limit;
     for (int s = 0; s < n; ++s) {
         launch_round_begin(c->d, c->stream);
-        launch_grid(c->d, c->max_nodes, c->stream);
+        launch_grid(c->d, c->max_nodes, c->grid_threads, c->grid_flat, c->stream);
         launch_check(c->d, 0, 0, c->stream);
         for (int j = 1; j < limit; ++j) {
             launch_transfer(c->d, MODE_ITER_, 0, (int)c->total_blocks, c->stream);
-            launch_grid(c->d, c->max_nodes, c->stream);
+            launch_grid(c->d, c->max_nodes, c->grid_threads, c->grid_flat, c->stream);
             launch_check(c->d, 0, 0, c->stream);
         }
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -492,8 +507,8 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
     int rc = TSIM_OK;
     Dev d = c->d;
     int zero = 0;
-    const unsigned int gx = (unsigned int)((c->max_nodes + 255) / 256);
-    const dim3 grid_grid(gx, c->n_inst), grid_blk(256);
+    dim3 grid_grid, grid_blk;
+    grid_launch_shape(d, c->max_nodes, c->grid_threads, c->grid_flat, grid_grid, grid_blk);
     const dim3 tr_grid((unsigned int)c->total_blocks), tr_blk(NT);
     cudaGraphNode_t prev = nullptr;
     out.n = n;
@@ -511,7 +526,7 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
         rc = add_kernel(g, &n_r0, prev ? &prev : nullptr, prev ? 1 : 0, fn_round_begin(),
                         dim3((c->n_inst + 127) / 128), dim3(128), a_r0);
         if (rc) break;
-        rc = add_kernel(g, &n_grid, &n_r0, 1, fn_grid(), grid_grid, grid_blk, a_grid);
+        rc = add_kernel(g, &n_grid, &n_r0, 1, fn_grid(c->grid_flat), grid_grid, grid_blk, a_grid);
         if (rc) break;
         rc = add_kernel(g, &n_chk, &n_grid, 1, fn_check(), dim3(1), dim3(256), a_chk);
         if (rc) break;
@@ -525,7 +540,7 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
         cudaGraphNode_t b_tr, b_grid, b_chk;
         rc = add_kernel(body, &b_tr, nullptr, 0, fn_transfer(MODE_ITER_), tr_grid, tr_blk, a_tr, transfer_smem_bytes());
         if (rc) break;
-        rc = add_kernel(body, &b_grid, &b_tr, 1, fn_grid(), grid_grid, grid_blk, a_grid);
+        rc = add_kernel(body, &b_grid, &b_tr, 1, fn_grid(c->grid_flat), grid_grid, grid_blk, a_grid);
         if (rc) break;
         rc = add_kernel(body, &b_chk, &b_grid, 1, fn_check(), dim3(1), dim3(256), a_chk);
         if (rc) break;
@@ -583,32 +598,37 @@ static int harvest_stream(tsim_ctx *c)
     return TSIM_OK;
 }
 
-static const int CHUNK = 20;
+static int ensure_chunks(tsim_ctx *c)
+{
+    if (!c->chunks.empty()) return TSIM_OK;
+    c->chunks.resize(3);
+    for (int a = 0; a < 2; ++a) {
+        int rc = build_chunk(c, c->chunk_len, c->chunks[a]);
+        if (rc) return rc;
+    }
+    c->chunks[2].n = 0;
+    c->chunk_next = 0;
+    return TSIM_OK;
+}
 
 static int launch_substeps_graph(tsim_ctx *c, int n)
 {
-    if (c->chunks.empty()) {
-        c->chunks.resize(3);
-        for (int a = 0; a < 2; ++a) {
-            int rc = build_chunk(c, CHUNK, c->chunks[a]);
-            if (rc) return rc;
-        }
-        c->chunks[2].n = 0;
-        c->chunk_next = 0;
-    }
+    int rc = ensure_chunks(c);
+    if (rc) return rc;
+    const int L = c->chunk_len;
     int left = n;
-    while (left >= CHUNK) {
+    while (left >= L) {
         GraphChunk &g = c->chunks[c->chunk_next];
-        int rc = harvest(c, g);
+        rc = harvest(c, g);
         if (rc) return rc;
         CU(cudaGraphLaunch(g.exec, c->stream));
         g.pending = c->profile;
         c->chunk_next ^= 1;
-        left -= CHUNK;
+        left -= L;
     }
     if (left > 0) {
         GraphChunk &g = c->chunks[2];
-        int rc = harvest(c, g);
+        rc = harvest(c, g);
         if (rc) return rc;
         if (g.n != left || !g.exec) {
             if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -622,24 +642,35 @@ static int launch_substeps_graph(tsim_ctx *c, int n)
     return TSIM_OK;
 }
 
+static int check_steppable(tsim_ctx *c)
+{
+    for (int i = 0; i < c->n_inst; ++i)
+        if (!c->have_particles[i])
+            return fail(TSIM_ERR_STATE, "instance " + std::to_string(i) + " has no particles");
+    return pending_prologues(c);
+}
+
+// n >= 1 substeps with the current execution configuration
+static int step_n(tsim_ctx *c, int n)
+{
+    launch_set_end(c->d, n, c->stream);
+    CU(cudaGetLastError());
+    int rc = c->use_graph ? launch_substeps_graph(c, n) : launch_substeps_stream(c, n);
+    if (rc) return rc;
+    c->k_next += n;
+    c->par_next ^= (n & 1);
+    return TSIM_OK;
+}
+
 extern "C" int tsim_step(tsim_ctx *c, int n)
 {
     int rc = check_ctx(c, 0);
     if (rc) return rc;
     if (n < 0) return fail(TSIM_ERR_INVALID_ARG, "n_substeps must be >= 0");
     if (n == 0) return TSIM_OK;
-    for (int i = 0; i < c->n_inst; ++i)
-        if (!c->have_particles[i])
-            return fail(TSIM_ERR_STATE, "instance " + std::to_string(i) + " has no particles");
-    rc = pending_prologues(c);
+    rc = check_steppable(c);
     if (rc) return rc;
-    launch_set_end(c->d, n, c->stream);
-    CU(cudaGetLastError());
-    rc = c->use_graph ? launch_substeps_graph(c, n) : launch_substeps_stream(c, n);
-    if (rc) return rc;
-    c->k_next += n;
-    c->par_next ^= (n & 1);
-    return TSIM_OK;
+    return step_n(c, n);
 }
 
 static int latched(tsim_ctx *c)
@@ -851,4 +882,147 @@ extern "C" int tsim_kernel_time(tsim_ctx *c, int64_t *launches, double *total_ms
     c->prof_launches = 0;
     c->prof_ms = 0.0;
     return TSIM_OK;
+}
+
+// ---------------------------------------------------------------- execution configuration
+
+static bool valid_tuning(const tsim_tuning_t *t)
+{
+    return t && (t->grid_threads == 128 || t->grid_threads == 256 || t->grid_threads == 512) &&
+           (t->grid_flat == 0 || t->grid_flat == 1) && t->graph_chunk >= 1 && t->graph_chunk <= 200;
+}
+
+static void apply_tuning(tsim_ctx *c, int threads, int flat, int chunk)
+{
+    if (threads != c->grid_threads || flat != c->grid_flat || chunk != c->chunk_len) invalidate_graphs(c);
+    c->grid_threads = threads;
+    c->grid_flat = flat;
+    c->chunk_len = chunk;
+}
+
+extern "C" int tsim_set_tuning(tsim_ctx *c, const tsim_tuning_t *t)
+{
+    int rc = check_ctx(c, 0);
+    if (rc) return rc;
+    if (!valid_tuning(t))
+        return fail(TSIM_ERR_INVALID_ARG, "tuning: grid_threads in {128, 256, 512}, grid_flat in {0, 1}, "
+                                          "1 <= graph_chunk <= 200");
+    CU(cudaStreamSynchronize(c->stream));
+    for (auto &g : c->chunks)
+        if ((rc = harvest(c, g))) return rc;
+    apply_tuning(c, t->grid_threads, t->grid_flat, t->graph_chunk);
+    return TSIM_OK;
+}
+
+extern "C" int tsim_get_tuning(tsim_ctx *c, tsim_tuning_t *out)
+{
+    int rc = check_ctx(c, 0);
+    if (rc) return rc;
+    if (!out) return fail(TSIM_ERR_INVALID_ARG, "out is NULL");
+    out->grid_threads = c->grid_threads;
+    out->grid_flat = c->grid_flat;
+    out->graph_chunk = c->chunk_len;
+    out->us_per_mupdate = c->tuned_us;
+    return TSIM_OK;
+}
+
+// particle-updates done so far (sum over instances of passes x particles); synchronises
+static int updates_so_far(tsim_ctx *c, double *out)
+{
+    CU(cudaStreamSynchronize(c->stream));
+    std::vector<InstState> h(c->n_inst);
+    CU(cudaMemcpy(h.data(), c->d.ist, sizeof(InstState) * c->n_inst, cudaMemcpyDeviceToHost));
+    double u = 0.0;
+    for (int i = 0; i < c->n_inst; ++i) u += (double)h[i].passes_total * c->hinst[i].n_particles;
+    *out = u;
+    return TSIM_OK;
+}
+
+// n substeps with the given configuration, timed with events on the stream
+// (graph executables are built before the first event)
+static int timed_window(tsim_ctx *c, int threads, int flat, int chunk, int n, double *ms, double *upd)
+{
+    for (auto &g : c->chunks) {
+        int rc = harvest(c, g);
+        if (rc) return rc;
+    }
+    apply_tuning(c, threads, flat, chunk);
+    if (c->use_graph) {
+        int rc = ensure_chunks(c);
+        if (rc) return rc;
+    }
+    double u0 = 0.0, u1 = 0.0;
+    int rc = updates_so_far(c, &u0);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    cudaEventRecord(e0, c->stream);
+    rc = step_n(c, n);
+    cudaEventRecord(e1, c->stream);
+    if (rc == TSIM_OK) rc = updates_so_far(c, &u1);
+    float t = 0.f;
+    if (rc == TSIM_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+        rc = fail(TSIM_ERR_CUDA, "autotune: event timing failed");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    *ms += t;
+    *upd += u1 - u0;
+    return latched(c);
+}
+
+// Online autotuning: the n substeps are the simulation's own (the state
+// advances as with tsim_step(n); the candidates differ only in how the same
+// kernels are launched).  Two interleaved rounds time the six grid-update
+// launch shapes on windows of equal length, then the three graph chunk
+// lengths (graph mode) with the best shape; the fastest per particle-update
+// is kept and the rest of the n substeps run with it.
+extern "C" int tsim_autotune(tsim_ctx *c, int n, tsim_tuning_t *out)
+{
+    int rc = check_ctx(c, 0);
+    if (rc) return rc;
+    static const int shapes[6][2] = {{128, 0}, {256, 0}, {512, 0}, {128, 1}, {256, 1}, {512, 1}};
+    static const int chunks[3] = {10, 20, 40};
+    const int rounds = 2, nwin = 6 * rounds + (c->use_graph ? 3 : 0);
+    int win = n / nwin;
+    if (c->use_graph) win = win / 40 * 40;           // whole graph launches for every chunk length
+    if (win < (c->use_graph ? 40 : 2))
+        return fail(TSIM_ERR_INVALID_ARG, std::string("autotune needs n >= ") +
+                                              std::to_string(nwin * (c->use_graph ? 40 : 2)) + " substeps");
+    rc = check_steppable(c);
+    if (rc) return rc;
+    const int chunk0 = c->chunk_len;
+    double ms[6] = {0}, upd[6] = {0};
+    for (int r = 0; r < rounds; ++r)
+        for (int k = 0; k < 6; ++k) {
+            const int kk = (r & 1) ? 5 - k : k;      // alternate the order between rounds
+            rc = timed_window(c, shapes[kk][0], shapes[kk][1], chunk0, win, &ms[kk], &upd[kk]);
+            if (rc) return rc;
+        }
+    int best = 0;
+    for (int k = 1; k < 6; ++k)
+        if (ms[k] * upd[best] < ms[best] * upd[k]) best = k;
+    double best_us = 1e3 * ms[best] / std::max(upd[best] * 1e-6, 1e-30);
+    int best_chunk = chunk0;
+    if (c->use_graph) {
+        double cms[3] = {0}, cupd[3] = {0};
+        int bc = 0;
+        for (int k = 0; k < 3; ++k) {
+            rc = timed_window(c, shapes[best][0], shapes[best][1], chunks[k], win, &cms[k], &cupd[k]);
+            if (rc) return rc;
+            if (k > 0 && cms[k] * cupd[bc] < cms[bc] * cupd[k]) bc = k;
+        }
+        best_chunk = chunks[bc];
+        best_us = 1e3 * cms[bc] / std::max(cupd[bc] * 1e-6, 1e-30);
+    }
+    apply_tuning(c, shapes[best][0], shapes[best][1], best_chunk);
+    c->tuned_us = (float)best_us;
+    const int rest = n - nwin * win;
+    if (rest > 0) {
+        rc = step_n(c, rest);
+        if (rc) return rc;
+    }
+    if (out) tsim_get_tuning(c, out);
+    return latched(c);
 }

@@ -93,6 +93,10 @@ struct Dev {                       // device pointers (passed by value to kernel
     // id-ordered staging (for writes and reads of particle state)
     float *sx, *sv, *sC, *sF;
     uint32_t *stag;
+    // packed grid-update launch: per 128-node chunk (instance, its first chunk);
+    // every instance's node range is padded to a multiple of 512 nodes
+    const int2 *gchunk;
+    long long n_gchunk;
     int n_inst;
 };
 

@@ -69,13 +69,13 @@ __global__ void k_set_end(Dev d, long long n)
 
 // ---------------------------------------------------------------- grid update
 
-__global__ void __launch_bounds__(256) k_grid(Dev d)
+// Grid update of node t (x fastest) of instance inst: Eq. 5 + gravity, SDF
+// contact with Coulomb stick/slip, walls, base.
+__device__ __forceinline__ void grid_node(const Dev &d, int inst, long long t)
 {
-    const int inst = blockIdx.y;
     InstState *S = d.ist + inst;
     if (S->phase != 0) return;
     const Inst &I = d.inst[inst];
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     // first pass of the substep: empty the destination cell-block counters
     if (S->pass == 0 && t < I.nblocks) d.cnt[d.G->par_next ^ 1][I.block0 + t] = 0;
     const long long nn = (long long)I.nx * I.ny * I.nz;
@@ -112,6 +112,22 @@ __global__ void __launch_bounds__(256) k_grid(Dev d)
     }
     d.vel[I.node0 + t] = make_float4(V[0], V[1], V[2], 0.f);
     d.acc[I.node0 + t] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// one launch row per instance (blockIdx.y), sized by the largest instance
+__global__ void __launch_bounds__(512) k_grid(Dev d)
+{
+    grid_node(d, blockIdx.y, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// one 1-D launch over all instances' node ranges packed back to back (no
+// empty CTAs for the smaller instances of an uneven batch); a CTA of up to
+// 512 threads never straddles two instances
+__global__ void __launch_bounds__(512) k_grid_flat(Dev d)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int2 e = d.gchunk[g >> 7];
+    grid_node(d, e.x, g - ((long long)e.y << 7));
 }
 
 // ---------------------------------------------------------------- relative-rest check
@@ -935,10 +951,19 @@ static inline unsigned int cdiv(long long a, long long b) { return (unsigned int
 void launch_round_begin(const Dev &d, cudaStream_t s) { k_round_begin<<<(d.n_inst + 127) / 128, 128, 0, s>>>(d); }
 void launch_set_end(const Dev &d, long long n, cudaStream_t s) { k_set_end<<<1, 1, 0, s>>>(d, n); }
 
-void launch_grid(const Dev &d, long long max_nodes, cudaStream_t s)
+void grid_launch_shape(const Dev &d, long long max_nodes, int threads, int flat, dim3 &grid, dim3 &block)
 {
-    dim3 g(cdiv(max_nodes, 256), d.n_inst);
-    k_grid<<<g, 256, 0, s>>>(d);
+    block = dim3(threads);
+    if (flat) grid = dim3((unsigned int)(d.n_gchunk * 128 / threads));
+    else grid = dim3((unsigned int)cdiv(max_nodes, threads), d.n_inst);
+}
+
+void launch_grid(const Dev &d, long long max_nodes, int threads, int flat, cudaStream_t s)
+{
+    dim3 g, b;
+    grid_launch_shape(d, max_nodes, threads, flat, g, b);
+    if (flat) k_grid_flat<<<g, b, 0, s>>>(d);
+    else k_grid<<<g, b, 0, s>>>(d);
 }
 
 void launch_check(const Dev &d, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s)
@@ -1007,7 +1032,7 @@ void launch_indenter_height(const Dev &d, int inst, float *h, int W, int H, floa
 
 // kernel handles for graph construction
 void *fn_round_begin() { return (void *)k_round_begin; }
-void *fn_grid() { return (void *)k_grid; }
+void *fn_grid(int flat) { return flat ? (void *)k_grid_flat : (void *)k_grid; }
 void *fn_check() { return (void *)k_check; }
 void *fn_transfer(int mode)
 {

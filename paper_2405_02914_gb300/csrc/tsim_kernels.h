@@ -10,7 +10,8 @@ enum { MODE_PROLOGUE_ = 0, MODE_ITER_ = 1, MODE_COMMIT_ = 2 };
 
 void launch_round_begin(const Dev &d, cudaStream_t s);
 void launch_set_end(const Dev &d, long long n, cudaStream_t s);
-void launch_grid(const Dev &d, long long max_nodes, cudaStream_t s);
+void grid_launch_shape(const Dev &d, long long max_nodes, int threads, int flat, dim3 &grid, dim3 &block);
+void launch_grid(const Dev &d, long long max_nodes, int threads, int flat, cudaStream_t s);
 void launch_check(const Dev &d, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
 void launch_transfer(const Dev &d, int mode, int block_offset, int nblocks, cudaStream_t s);
 void launch_bin_staged(const Dev &d, int inst, int n, int par, cudaStream_t s);
@@ -26,7 +27,7 @@ cudaError_t setup_kernels();
 size_t transfer_smem_bytes();
 
 void *fn_round_begin();
-void *fn_grid();
+void *fn_grid(int flat);
 void *fn_check();
 void *fn_transfer(int mode);
 

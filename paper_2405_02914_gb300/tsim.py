@@ -24,7 +24,8 @@ EXPORTS = ["tsim_create", "tsim_set_solver", "tsim_set_indenter", "tsim_set_traj
            "tsim_write_particles", "tsim_set_substep", "tsim_step", "tsim_read_particles",
            "tsim_read_grid", "tsim_read_surface", "tsim_read_markers", "tsim_read_log", "tsim_sync",
            "tsim_stats", "tsim_use_graph", "tsim_profile", "tsim_kernel_time", "tsim_last_error",
-           "tsim_destroy", "tsim_p2g_noalloc", "tsim_read_displacement", "tsim_read_indenter_height"]
+           "tsim_destroy", "tsim_p2g_noalloc", "tsim_read_displacement", "tsim_read_indenter_height",
+           "tsim_set_tuning", "tsim_get_tuning", "tsim_autotune"]
 
 
 class TsimError(RuntimeError):
@@ -62,6 +63,15 @@ class Stats(C.Structure):
                 ("status", C.c_uint32), ("n_inst", C.c_int32)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("grid_threads", C.c_int), ("grid_flat", C.c_int), ("graph_chunk", C.c_int),
+                ("us_per_mupdate", C.c_float)]
+
+    def as_dict(self):
+        return {"grid_threads": self.grid_threads, "grid_flat": self.grid_flat, "graph_chunk": self.graph_chunk,
+                "us_per_mupdate": self.us_per_mupdate}
+
+
 _lib = None
 
 
@@ -97,6 +107,9 @@ def load():
             "tsim_destroy": (None, [vp]),
             "tsim_p2g_noalloc": (C.c_int, [P(GelDesc), P(MaterialDesc), C.c_float, vp, vp, vp, vp, C.c_int,
                                            vp, vp]),
+            "tsim_set_tuning": (C.c_int, [vp, P(Tuning)]),
+            "tsim_get_tuning": (C.c_int, [vp, P(Tuning)]),
+            "tsim_autotune": (C.c_int, [vp, C.c_int, P(Tuning)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -320,6 +333,24 @@ def tsim_kernel_time(ctx):
     ms = C.c_double()
     _check(load().tsim_kernel_time(ctx, C.byref(n), C.byref(ms)))
     return n.value, ms.value
+
+
+def tsim_set_tuning(ctx, grid_threads=256, grid_flat=0, graph_chunk=20):
+    t = Tuning(int(grid_threads), int(grid_flat), int(graph_chunk), 0.0)
+    _check(load().tsim_set_tuning(ctx, C.byref(t)))
+
+
+def tsim_get_tuning(ctx) -> dict:
+    t = Tuning()
+    _check(load().tsim_get_tuning(ctx, C.byref(t)))
+    return t.as_dict()
+
+
+def tsim_autotune(ctx, n) -> dict:
+    """Advance n substeps (as tsim_step) while choosing the fastest launch configuration."""
+    t = Tuning()
+    _check(load().tsim_autotune(ctx, int(n), C.byref(t)))
+    return t.as_dict()
 
 
 def tsim_destroy(ctx):

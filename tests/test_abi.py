@@ -46,13 +46,14 @@ def test_struct_layouts_match_header(tmp_path):
                     'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(tsim_gel_desc),'
                     'sizeof(tsim_material), sizeof(tsim_indenter_desc), sizeof(tsim_keyframe),'
                     'sizeof(tsim_solver_desc), sizeof(tsim_stats_t), offsetof(tsim_indenter_desc, perm));'
+                    'printf("%zu %zu\\n", sizeof(tsim_tuning_t), offsetof(tsim_tuning_t, us_per_mupdate));'
                     'return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
     got = [int(a) for a in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [C.sizeof(tsim.GelDesc), C.sizeof(tsim.MaterialDesc), C.sizeof(tsim.IndenterDesc),
             C.sizeof(tsim.Keyframe), C.sizeof(tsim.SolverDesc), C.sizeof(tsim.Stats),
-            tsim.IndenterDesc.perm.offset]
+            tsim.IndenterDesc.perm.offset, C.sizeof(tsim.Tuning), tsim.Tuning.us_per_mupdate.offset]
     assert got == want
 
 
@@ -71,6 +72,10 @@ def test_invalid_arguments_rejected_without_gpu():
     g.cx, g.cy, g.cz, g.nx, g.ny, g.nz, g.ox, g.oy, g.oz, g.ppc, g.dx = 4, 4, 4, 13, 12, 16, 4, 4, 4, 8, 1e-3
     m.E, m.nu, m.rho = 1e5, 0.4, 1000.0
     assert L.tsim_create(1, C.byref(g), C.byref(m), None, C.byref(out)) == 1
+    t = tsim.Tuning(256, 0, 20, 0.0)
+    assert L.tsim_set_tuning(None, C.byref(t)) == 1
+    assert L.tsim_get_tuning(None, C.byref(t)) == 1
+    assert L.tsim_autotune(None, 600, None) == 1
     L.tsim_destroy(None)
 
 

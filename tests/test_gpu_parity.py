@@ -401,3 +401,60 @@ def test_displacement_and_indenter_height_match_oracle(kind):
     assert np.median(np.abs(h[hit] - ho[hit])) < 1e-3 * sc.gel.dx
     assert np.abs(h[hit] - ho[hit]).max() < 0.05 * sc.gel.dx
     assert np.all(h[~hit] == np.float32(clip))
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_autotune_advances_like_step_and_keeps_a_candidate(graph):
+    """tsim_autotune(n) advances the state as tsim_step(n) does (the candidates
+    only change launch shapes and graph chunking) and keeps one candidate."""
+    # three uneven pads (common dt) with a gentle press and slide
+    scenes = [I.scene_small(cx=16, cy=12, cz=4, press=0.1e-3, n_press=300, slip=0.1e-3, n_slip=300, seed=1),
+              I.scene_small(cx=8, cy=8, cz=4, press=0.08e-3, n_press=300, slip=0.05e-3, n_slip=300, mu=0.3,
+                            seed=2),
+              I.scene_small(cx=24, cy=20, cz=6, press=0.12e-3, n_press=300, rotate=0.1, n_rot=300, seed=3)]
+    n = 600 if graph else 48
+    states = [_init(sc) for sc in scenes]
+    a = T.Sim(scenes, use_graph=graph, states=states)
+    b = T.Sim(scenes, use_graph=graph, states=states)
+    a.step(n)
+    T.tsim_sync(a.ctx)
+    cfg = T.tsim_autotune(b.ctx, n)
+    assert cfg["grid_threads"] in (128, 256, 512) and cfg["grid_flat"] in (0, 1)
+    assert cfg["us_per_mupdate"] > 0
+    if graph:
+        assert cfg["graph_chunk"] in (10, 20, 40)
+    assert T.tsim_stats(b.ctx).substeps == n
+    kept = T.tsim_get_tuning(b.ctx)
+    assert {k: kept[k] for k in ("grid_threads", "grid_flat", "graph_chunk")} == \
+        {k: cfg[k] for k in ("grid_threads", "grid_flat", "graph_chunk")}
+    a.step(40)
+    b.step(40)
+    for i, sc in enumerate(scenes):
+        xa = T.tsim_read_particles(a.ctx, i, sc.gel.n_particles)[0]
+        xb = T.tsim_read_particles(b.ctx, i, sc.gel.n_particles)[0]
+        assert np.abs(xa - xb).max() < POS_TOL * sc.gel.dx, i
+    a.close()
+    b.close()
+    c = T.Sim(scenes, use_graph=graph, states=states)
+    try:
+        with pytest.raises(T.TsimError):
+            T.tsim_autotune(c.ctx, 10)                      # too few substeps for the windows
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("threads,flat", [(512, 1), (128, 0)])
+def test_grid_launch_shapes_match_oracle(threads, flat):
+    scenes = [I.scene_small(cx=16, cy=12, cz=4, press=0.1e-3, n_press=150, seed=4),
+              I.scene_small(cx=8, cy=12, cz=4, press=0.08e-3, n_press=100, slip=0.05e-3, n_slip=50, seed=5),
+              I.scene_small(cx=20, cy=16, cz=5, press=0.1e-3, n_press=150, seed=6)]
+    states = [_init(sc) for sc in scenes]
+    sim = T.Sim(scenes, use_graph=True, states=states)
+    T.tsim_set_tuning(sim.ctx, threads, flat, 10)
+    sim.step(150)
+    for i, sc in enumerate(scenes):
+        st, s, ind = _oracle(sc, states[i])
+        O.run(s, ind, sc.keyframes, 0, 150, st)
+        x, _, _, _ = T.tsim_read_particles(sim.ctx, i, sc.gel.n_particles)
+        assert np.abs(x - st.x).max() < POS_TOL * sc.gel.dx, i
+    sim.close()
