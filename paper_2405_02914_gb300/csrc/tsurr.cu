@@ -5,6 +5,7 @@
 // indicator channel; Adam.  Architecture and loss: include/tsurr.h.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>   // CUtensorMap and the cuTensorMapEncodeTiled signature (entry point fetched at run time)
 
 #include <cmath>
 #include <cstdint>
@@ -82,37 +83,42 @@ struct Conv {
 
 // ---------------------------------------------------------------- forward on tcgen05
 
-// The forward runs on the 5th-generation tensor cores: one CTA computes 128
-// output pixels x all cout channels, D[128][cout] in tensor memory (TMEM).
-// Operands are staged in shared memory by cp.async (the im2col gather with
-// zero fill for the padding), in the no-swizzle K-major layout of 8-row x
-// 16-byte core matrices; one elected thread issues tcgen05.mma (M = 128,
-// N = cout, K = 16) and tracks completion with tcgen05.commit on a per-stage
-// mbarrier; the epilogue reads D back with tcgen05.ld (warp w owns TMEM lanes
-// 32w..32w+31, i.e. its 32 pixels) and fuses bias, skip and ReLU.
-constexpr int TC_M = 128;          // output pixels per CTA (UMMA M)
-constexpr int TC_MAX_STAGES = 16;  // shared-memory stages of 64 K each (4 UMMAs of K = 16); k-tiles are
-                                   // loaded stages - 2 ahead, so a stage is refilled only after the
-                                   // UMMAs that read it two iterations ago have completed
-constexpr uint32_t TC_LBO = 128;   // bytes between the two K halves (core matrices) of a K16 slice
-constexpr uint32_t TC_SBO = 256;   // bytes between 8-row groups of a K16 slice
+// The forward convolutions run on the 5th-generation tensor cores as
+// implicit GEMMs, D[pixels][cout] = A[pixels][9 cin] B[cout][9 cin]^T, with
+// UMMA M = 128 pixels, N = cout, K = 16 per instruction and the accumulator in
+// tensor memory (TMEM).  Both operands are fetched by TMA tensor copies that
+// land directly in the UMMA no-swizzle K-major layout (8-row x 16-byte core
+// matrices): the A tile of one 8-channel chunk of one tap is a 4-D box
+// {8 channels, bw x bh pixels, 1 image} of the NHWC input at the tap's offset
+// (zero fill outside the image = the convolution's zero padding; stride-2
+// layers sample every other pixel through the tensor map's element strides),
+// the B tile a 2-D box {8 k, cout rows} of the weights.  An output tile is a
+// bw x bh rectangle of one image (bw * bh <= 128 rows of M).  Layers that read
+// a nearest x2 upsampling of their input are split into the four output
+// phases (2i + a, 2j + b): for a phase, tap (ky, kx) reads low-resolution
+// pixel (i + floor((a + ky - 1) / 2), j + floor((b + kx - 1) / 2)), so each
+// phase is a stride-1 gather of the low-resolution input with the same nine
+// taps and weights (the arithmetic is that of the upsampled convolution).
+constexpr int TC_M = 128;          // rows of M per tile (UMMA M)
+constexpr int TC_MAX_STAGES = 16;  // shared-memory stages of 64 K each (4 UMMAs of K = 16)
 constexpr int TC_WAIT = 1 << 22;   // polls before a wait gives up
+constexpr int TC_THREADS = 192;    // warp 0 issues TMA, warp 1 the UMMAs, warps 2-5 run the epilogue
 
-__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t bytes)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void bar_init_n(uint32_t bar, uint32_t n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity)
 {
     for (int it = 0; it < TC_WAIT; ++it) {
@@ -127,13 +133,35 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
-// offsets in 16-byte units, descriptor version 1 (bits 46-48 = 0b001), no
-// swizzle (bits 61-63 = 0).
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr)
+// TMA tensor loads into shared memory, completion counted on an mbarrier
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
 {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(TC_LBO >> 4) << 16) | ((uint64_t)(TC_SBO >> 4) << 32) |
-           (1ull << 46);
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                 "%3, %4, %5}], [%6];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                 "%3}], [%4];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand whose rows are `row`
+// bytes of K (32, 64 or 128) in the matching swizzled layout that TMA writes
+// (8-row atoms of 8 x row bytes, 16-byte units XOR-permuted within a row by
+// the row index): start address in 16-byte units, leading byte offset unused
+// (1), stride byte offset = 8 rows, descriptor version 1 (bits 46-48 = 0b001),
+// layout type at bits 61-63 (6: 32-byte, 4: 64-byte, 2: 128-byte swizzle).
+// A K16 slice j of the row starts 32 j bytes into it.
+__device__ __forceinline__ uint64_t umma_desc_sw(uint32_t addr, uint32_t row)
+{
+    const uint64_t layout = row == 128 ? 2 : (row == 64 ? 4 : 6);
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)((8 * row) >> 4) << 32) | (1ull << 46) |
+           (layout << 61);
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
@@ -168,36 +196,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// dynamic shared memory of k_conv_fwd_tc for cout channels: as many stages
-// as fit in 220 KB (3 .. 16)
+// A chunk is cw = min(cin, 64) channels of one tap (an A box of 128 rows x
+// 2 cw bytes and a B box of cout rows x 2 cw bytes, each starting on a
+// 1024-byte boundary, the swizzle atom); a stage holds 64 / cw chunks, so
+// every stage carries K = 64; as many stages as fit in 220 KB.
 constexpr uint32_t TC_SMEM_MAX = 220u * 1024u;
-__host__ __device__ inline uint32_t tc_stage_bytes(int cout) { return 4u * (TC_M * 32u + (uint32_t)cout * 32u); }
-__host__ __device__ inline int tc_stages(int cout)
+__host__ __device__ inline uint32_t tc_a_slot(int cw) { return (uint32_t)TC_M * 2u * (uint32_t)cw; }
+__host__ __device__ inline uint32_t tc_b_slot(int cout, int cw)
 {
-    const int s = (int)((TC_SMEM_MAX - 2048u) / tc_stage_bytes(cout));
+    return ((uint32_t)cout * 2u * (uint32_t)cw + 1023u) & ~1023u;
+}
+__host__ __device__ inline uint32_t tc_stage_bytes(int cout, int cw)
+{
+    return (uint32_t)(64 / cw) * (tc_a_slot(cw) + tc_b_slot(cout, cw));
+}
+__host__ __device__ inline int tc_stages(int cout, int cw)
+{
+    const int s = (int)((TC_SMEM_MAX - 2048u) / tc_stage_bytes(cout, cw));
     return s < 3 ? 3 : (s > TC_MAX_STAGES ? TC_MAX_STAGES : s);
 }
-__host__ __device__ inline uint32_t tc_smem_bytes(int cout)
+__host__ __device__ inline uint32_t tc_smem_bytes(int cout, int cw)
 {
-    return (uint32_t)tc_stages(cout) * tc_stage_bytes(cout) + 1024 + 16 * TC_MAX_STAGES + 64;
+    return (uint32_t)tc_stages(cout, cw) * tc_stage_bytes(cout, cw) + 1024 + 16 * TC_MAX_STAGES + 64;
 }
-
-__device__ __forceinline__ void cp_async_arrive(uint32_t bar)
-{
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void bar_init_n(uint32_t bar, uint32_t n)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(n) : "memory");
-}
-
-constexpr int TC_THREADS = 288;    // warps 0-3 load, warps 4-7 run the epilogue, warp 8 issues the UMMAs
-
-__device__ __forceinline__ void bar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
 // TMEM columns for two accumulators of n columns (a power of two >= 32)
 __host__ __device__ inline uint32_t tc_tmem_cols(int n)
 {
@@ -206,42 +227,56 @@ __host__ __device__ inline uint32_t tc_tmem_cols(int n)
     return c;
 }
 
-// Persistent, warp-specialised: each CTA walks output tiles of 128 pixels
-// (tile = blockIdx.x, += gridDim.x).  The loaders fill a ring of stages of
-// 64 K with cp.async and signal full[s] when their copies land
-// (cp.async.mbarrier.arrive.noinc, 128 arrivals); the issuing thread waits on
-// full[s], fences the generic-proxy writes against the tensor core's
-// async-proxy reads, issues the stage's UMMAs into accumulator (tile & 1) and
-// commits them to empty[s]; at the end of a tile it commits to accf[b].  The
-// epilogue warps drain accumulator b with tcgen05.ld while the next tile
-// accumulates into the other one, then release it on acce[b].  The issuing
-// warp never has copies in flight, so its proxy fence does not wait for the
-// loads of later stages.
-__global__ void __launch_bounds__(TC_THREADS, 1) k_conv_fwd_tc(Conv c, int *err)
+struct TcConv {
+    int N, cin, K, cw, nkt;        // cout, input channels, 9 cin, channels per chunk, stages per tile
+    int up, stride;                // nearest x2 input (4 output phases) or the input sampling stride
+    int gw, gh;                    // tile grid: output size, or the low-resolution input size when up
+    int bw, bh, ntx, nty, nph;     // tile rectangle, tiles per image row/column, phases (1 or 4)
+    long long ntiles;
+    int hout, wout;
+    const float *bias;
+    const bf16 *skip;              // added before the ReLU (same shape as the output) or null
+    int relu;
+    bf16 *out;                     // [B][hout][wout][N] BF16, or
+    float *out32;                  // FP32 output keeping the first out32_ch channels
+    int out32_ch;
+};
+
+// Persistent, warp-specialised: each CTA walks output tiles (tile =
+// blockIdx.x, += gridDim.x).  The TMA thread fills a ring of stages, one
+// expect_tx arrival per stage on full[s]; the UMMA thread waits on full[s],
+// issues the stage's UMMAs into accumulator (tile & 1) and commits them to
+// empty[s] (which the TMA thread waits on before refilling the stage) and, at
+// the end of a tile, to accf[b].  The epilogue warps drain accumulator b with
+// tcgen05.ld while the next tile accumulates into the other, then release it
+// on acce[b].  Every wait is bounded; a wait that gives up sets *err.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_conv_fwd_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcConv c, int *err)
 {
     extern __shared__ unsigned char tc_raw[];
-    const int N = c.cout, K = 9 * c.cin, M = c.B * c.hout * c.wout;
-    const int nk16 = K / 16, nkt = (nk16 + 3) / 4, ntiles = (M + TC_M - 1) / TC_M;
-    const uint32_t a_bytes = TC_M * 32, b_bytes = (uint32_t)N * 32, stage_bytes = tc_stage_bytes(N);
-    const int NS = tc_stages(N);
+    const int N = c.N, cw = c.cw;
+    const uint32_t row = 2u * (uint32_t)cw, stage_bytes = tc_stage_bytes(N, cw);
+    const uint32_t a_slot = tc_a_slot(cw), b_slot = tc_b_slot(N, cw), b_base = (uint32_t)(64 / cw) * a_slot;
+    const uint32_t a_box = (uint32_t)(c.bw * c.bh) * row, b_box = (uint32_t)N * row;
+    const int NS = tc_stages(N, cw), per_tap = c.cin / cw, kslices = cw / 16, cps = 64 / cw;
+    const int nchunks = 9 * per_tap;
     // stages 1024-byte aligned; then full[16], empty[16], accf[2], acce[2], the TMEM address
-    const uint32_t raw = saddr(tc_raw);
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(tc_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    unsigned char *stages = tc_raw + (base - raw);
     const uint32_t full = base + NS * stage_bytes, empty = full + 8 * TC_MAX_STAGES;
     const uint32_t accf = empty + 8 * TC_MAX_STAGES, acce = accf + 16, tslot = acce + 16;
-    const uint32_t *tslot_p = reinterpret_cast<const uint32_t *>(stages + (tslot - base));
+    const uint32_t *tslot_p = reinterpret_cast<const uint32_t *>(tc_raw + (tslot - raw));
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const uint32_t ncols = tc_tmem_cols(N);
 
-    if (warp == 8) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (t == 0) {
         for (int s = 0; s < NS; ++s) {
-            bar_init_n(full + 8 * s, 128);
+            bar_init_n(full + 8 * s, 1);
             bar_init_n(empty + 8 * s, 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -256,61 +291,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_fwd_tc(Conv c, int *err)
     const uint32_t tmem = *tslot_p;
     bool ok = true;
 
-    if (warp < 4) {
-        // loader: thread t moves 16-byte chunk q = t & 7 of rows (t >> 3) + 16 i;
-        // chunk q is K half (q & 1) of K16 slice (q >> 1) of the stage
-        const int q = t & 7, slice = q >> 1, half = q & 1, r0 = t >> 3;
-        uint32_t g = 0;                                // k-tiles loaded so far (ring position)
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            int rb[8], ry[8], rx[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int m = tile * TC_M + r0 + 16 * i;
-                if (m < M) {
-                    rx[i] = m % c.wout;
-                    ry[i] = (m / c.wout) % c.hout;
-                    rb[i] = m / (c.wout * c.hout);
-                } else {
-                    rb[i] = -1;
-                    ry[i] = rx[i] = 0;
-                }
-            }
-            for (int kt = 0; kt < nkt; ++kt, ++g) {
-                const uint32_t s = g % NS;
-                // the stage was last read by the UMMAs of ring position g - NS
-                if (g >= (uint32_t)NS && !bar_wait(empty + 8 * s, ((g / NS) - 1) & 1)) {
-                    ok = false;
-                    break;
-                }
-                const int k16 = kt * 4 + slice;
-                if (k16 < nk16) {
-                    const int k = k16 * 16 + half * 8;
-                    const int kk = k / c.cin, ci = k % c.cin, ky = kk / 3, kx = kk % 3;
-                    const uint32_t sa = base + s * stage_bytes + slice * a_bytes + half * 128;
-                    const uint32_t sb = base + s * stage_bytes + 4 * a_bytes + slice * b_bytes + half * 128;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int r = r0 + 16 * i;
-                        int iy = ry[i] * c.stride + ky - 1, ix = rx[i] * c.stride + kx - 1;
-                        const bool v = rb[i] >= 0 && iy >= 0 && iy < c.hl && ix >= 0 && ix < c.wl;
-                        if (c.up) { iy >>= 1; ix >>= 1; }
-                        const bf16 *src =
-                            v ? c.in + (((size_t)rb[i] * c.hin + iy) * c.win + ix) * c.cin + ci : c.in;
-                        cp_async16(sa + (r >> 3) * TC_SBO + (r & 7) * 16, src, v ? 16u : 0u);
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;                                // k-tiles loaded so far (ring position)
+            for (long long tile = blockIdx.x; tile < c.ntiles && ok; tile += gridDim.x) {
+                long long rest = tile;
+                const int ph = (int)(rest % c.nph);
+                rest /= c.nph;
+                const int tx = (int)(rest % c.ntx);
+                rest /= c.ntx;
+                const int ty = (int)(rest % c.nty);
+                const int b = (int)(rest / c.nty);
+                const int X0 = tx * c.bw, Y0 = ty * c.bh, pa = ph >> 1, pb = ph & 1;
+                for (int kt = 0; kt < c.nkt; ++kt, ++g) {
+                    const uint32_t s = g % NS;
+                    // the stage was last read by the UMMAs of ring position g - NS
+                    if (g >= (uint32_t)NS && !bar_wait(empty + 8 * s, ((g / NS) - 1) & 1)) {
+                        ok = false;
+                        break;
                     }
-                    for (int n = r0; n < N; n += 16)
-                        cp_async16(sb + (n >> 3) * TC_SBO + (n & 7) * 16, c.w + (size_t)n * K + k, 16u);
+                    const int nq = min(cps, nchunks - kt * cps);     // chunks in this stage
+                    bar_expect_tx(full + 8 * s, (uint32_t)nq * (a_box + b_box));
+                    const uint32_t sa = base + s * stage_bytes, sb = sa + b_base;
+                    for (int q = 0; q < nq; ++q) {
+                        const int ch = kt * cps + q;
+                        const int tap = ch / per_tap, ci = (ch - tap * per_tap) * cw, ky = tap / 3, kx = tap - 3 * ky;
+                        int x, y;
+                        if (c.up) {
+                            x = X0 + ((pb + kx + 1) >> 1) - 1;
+                            y = Y0 + ((pa + ky + 1) >> 1) - 1;
+                        } else {
+                            x = c.stride * X0 + kx - 1;
+                            y = c.stride * Y0 + ky - 1;
+                        }
+                        tma_load_4d(sa + q * a_slot, &tmA, ci, x, y, b, full + 8 * s);
+                        tma_load_2d(sb + q * b_slot, &tmB, tap * c.cin + ci, 0, full + 8 * s);
+                    }
                 }
-                cp_async_arrive(full + 8 * s);
             }
         }
-        cp_async_wait<0>();
-    } else if (warp == 8) {
+    } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = umma_idesc(TC_M, N);
             uint32_t g = 0;
             int it = 0;
-            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+            for (long long tile = blockIdx.x; tile < c.ntiles && ok; tile += gridDim.x, ++it) {
                 const int b = it & 1;
                 // accumulator b was last drained by the epilogue of tile it - 2
                 if (it >= 2 && !bar_wait(acce + 8 * b, ((it >> 1) - 1) & 1)) {
@@ -319,28 +344,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_fwd_tc(Conv c, int *err)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * N);
-                for (int kt = 0; kt < nkt; ++kt, ++g) {
+                for (int kt = 0; kt < c.nkt; ++kt, ++g) {
                     const uint32_t s = g % NS;
                     if (!bar_wait(full + 8 * s, (g / NS) & 1)) {
                         ok = false;
                         break;
                     }
-                    fence_proxy_async();
                     tc_fence_after();
-                    const uint32_t sa = base + s * stage_bytes, sb = sa + 4 * a_bytes;
-                    for (int j = 0; j < 4 && kt * 4 + j < nk16; ++j)
-                        umma_bf16(d, umma_desc(sa + j * a_bytes), umma_desc(sb + j * b_bytes), idesc,
-                                  (kt | j) != 0);
+                    const uint32_t sa = base + s * stage_bytes, sb = sa + b_base;
+                    const int nq = min(cps, nchunks - kt * cps);
+                    for (int q = 0; q < nq; ++q)
+                        for (int j = 0; j < kslices; ++j)
+                            umma_bf16(d, umma_desc_sw(sa + q * a_slot + 32 * j, row),
+                                      umma_desc_sw(sb + q * b_slot + 32 * j, row), idesc, (kt | q | j) != 0);
                     umma_commit(empty + 8 * s);
                 }
                 umma_commit(accf + 8 * b);      // tracks every UMMA of the tile
             }
         }
     } else {
-        // epilogue: warp 4 + e reads TMEM lanes 32e .. 32e + 31 = pixels 32e .. 32e + 31 of the tile
-        const int e = warp - 4;
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows 32 (w % 4) .. + 31
+        const int e = warp & 3;
         int it = 0;
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+        for (long long tile = blockIdx.x; tile < c.ntiles && ok; tile += gridDim.x, ++it) {
             const int b = it & 1;
             // warp-uniform decision: tcgen05.ld below must be executed by all 32 lanes
             if (!__all_sync(0xffffffffu, bar_wait(accf + 8 * b, (it >> 1) & 1))) {
@@ -348,16 +374,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_fwd_tc(Conv c, int *err)
                 break;
             }
             tc_fence_after();
-            const int row = tile * TC_M + e * 32 + lane;
+            long long rest = tile;
+            const int ph = (int)(rest % c.nph);
+            rest /= c.nph;
+            const int tx = (int)(rest % c.ntx);
+            rest /= c.ntx;
+            const int ty = (int)(rest % c.nty);
+            const int bimg = (int)(rest / c.nty);
+            const int r = e * 32 + lane;
+            const int gx = tx * c.bw + r % c.bw, gy = ty * c.bh + r / c.bw;
+            const bool valid = r < c.bw * c.bh && gx < c.gw && gy < c.gh;
+            const int oy = c.up ? 2 * gy + (ph >> 1) : gy, ox = c.up ? 2 * gx + (ph & 1) : gx;
+            const long long pix = ((long long)bimg * c.hout + oy) * c.wout + ox;
             for (int c0 = 0; c0 < N; c0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(b * N + c0), r);
-                if (row >= M) continue;
+                uint32_t rr[16];
+                tmem_ld16(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(b * N + c0), rr);
+                if (!valid) continue;
                 float v[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) + c.bias[c0 + j];
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(rr[j]) + c.bias[c0 + j];
                 if (c.skip) {
-                    const uint4 *sp = reinterpret_cast<const uint4 *>(c.skip + (size_t)row * N + c0);
+                    const uint4 *sp = reinterpret_cast<const uint4 *>(c.skip + pix * N + c0);
                     uint4 s2[2] = {sp[0], sp[1]};
                     const bf16 *se = reinterpret_cast<const bf16 *>(s2);
 #pragma unroll
@@ -368,14 +405,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_fwd_tc(Conv c, int *err)
                     for (int j = 0; j < 16; ++j) v[j] = fmaxf(v[j], 0.f);
                 }
                 if (c.out32) {
-                    for (int j = 0; j < 16 && c0 + j < c.out32_ch; ++j)
-                        c.out32[(size_t)row * c.out32_ch + c0 + j] = v[j];
+                    for (int j = 0; j < 16 && c0 + j < c.out32_ch; ++j) c.out32[pix * c.out32_ch + c0 + j] = v[j];
                 } else {
                     uint4 o2[2];
                     bf16 *oe = reinterpret_cast<bf16 *>(o2);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) oe[j] = f2bf(v[j]);
-                    uint4 *op = reinterpret_cast<uint4 *>(c.out + (size_t)row * N + c0);
+                    uint4 *op = reinterpret_cast<uint4 *>(c.out + pix * N + c0);
                     op[0] = o2[0];
                     op[1] = o2[1];
                 }
@@ -386,7 +422,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_fwd_tc(Conv c, int *err)
     }
     tc_fence_before();
     const bool all_ok = __syncthreads_and(ok);
-    if (warp == 8)
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
     if (t == 0 && !all_ok) atomicOr(err, 1);
 }
@@ -650,6 +686,8 @@ struct tsurr_net {
     float *xbuf = nullptr, *tbuf = nullptr, *mbuf = nullptr;
     int *err = nullptr;          // set by a kernel whose bounded wait gave up
     int num_sms = 1;
+    CUtensorMap tmA[NL], tmB[NL];   // TMA maps of each layer's input (at max_batch) and BF16 weights
+    TcConv tc[NL];                  // tile geometry of each layer's forward
     std::vector<void *> allocs;
 };
 
@@ -699,6 +737,71 @@ static Conv conv_of(const tsurr_net *n, int L, int B)
     c.out = n->act[L + 1];
     c.out32 = nullptr;
     return c;
+}
+
+// TMA maps and tile geometry of the nine forward convolutions (once per net)
+static bool setup_forward(tsurr_net *n, std::string *why)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            *why = "cuTensorMapEncodeTiled is not available";
+            return false;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    for (int L = 0; L < NL; ++L) {
+        TcConv &c = n->tc[L];
+        memset(&c, 0, sizeof(c));
+        const int hin = n->hin[L], win = n->win[L], cin = n->cin[L], cout = n->cout[L];
+        c.N = cout;
+        c.cin = cin;
+        c.K = 9 * cin;
+        c.cw = std::min(cin, 64);
+        c.nkt = (9 * (cin / c.cw) + (64 / c.cw) - 1) / (64 / c.cw);
+        c.up = n->up[L];
+        c.stride = n->stride[L];
+        c.hout = (c.up ? 2 * hin : hin) / c.stride;
+        c.wout = (c.up ? 2 * win : win) / c.stride;
+        c.gw = c.up ? win : c.wout;
+        c.gh = c.up ? hin : c.hout;
+        c.bw = std::min(c.gw, TC_M);
+        c.bh = std::max(1, std::min(c.gh, TC_M / c.bw));
+        c.ntx = (c.gw + c.bw - 1) / c.bw;
+        c.nty = (c.gh + c.bh - 1) / c.bh;
+        c.nph = c.up ? 4 : 1;
+        c.relu = n->relu[L];
+        const cuuint32_t es = (cuuint32_t)(c.up ? 1 : c.stride);
+        const cuuint64_t gdim[4] = {(cuuint64_t)cin, (cuuint64_t)win, (cuuint64_t)hin, (cuuint64_t)n->maxB};
+        const cuuint64_t gstr[3] = {(cuuint64_t)cin * 2, (cuuint64_t)win * cin * 2, (cuuint64_t)hin * win * cin * 2};
+        const cuuint32_t box[4] = {(cuuint32_t)c.cw, (cuuint32_t)c.bw * es, (cuuint32_t)c.bh * es, 1};
+        const CUtensorMapSwizzle swz = c.cw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                                  : (c.cw == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+        const cuuint32_t estr[4] = {1, es, es, 1};
+        CUresult r = encode(&n->tmA[L], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)n->act[n->src[L]], gdim, gstr, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            *why = "tensor map of layer " + std::to_string(L) + " input: error " + std::to_string((int)r);
+            return false;
+        }
+        const cuuint64_t wdim[2] = {(cuuint64_t)c.K, (cuuint64_t)cout};
+        const cuuint64_t wstr[1] = {(cuuint64_t)c.K * 2};
+        const cuuint32_t wbox[2] = {(cuuint32_t)c.cw, (cuuint32_t)cout};
+        const cuuint32_t westr[2] = {1, 1};
+        r = encode(&n->tmB[L], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)n->wb[L], wdim, wstr, wbox, westr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            *why = "tensor map of layer " + std::to_string(L) + " weights: error " + std::to_string((int)r);
+            return false;
+        }
+    }
+    return true;
 }
 
 extern "C" int tsurr_create(int max_batch, int height, int width, void *stream, tsurr_net **out)
@@ -795,6 +898,12 @@ extern "C" int tsurr_create(int max_batch, int height, int width, void *stream, 
         delete n;
         return sfail(TSIM_ERR_CUDA, "tsurr_create: initialisation failed");
     }
+    std::string why;
+    if (!setup_forward(n, &why)) {
+        for (void *p : n->allocs) cudaFree(p);
+        delete n;
+        return sfail(TSIM_ERR_CUDA, "tsurr_create: " + why);
+    }
     *out = n;
     return TSIM_OK;
 }
@@ -852,15 +961,19 @@ static int run_forward(tsurr_net *n, const float *x, int B)
     const long long npix = (long long)B * n->H * n->W;
     k_input<<<cdiv(npix * CIN_PAD, 256), 256, 0, n->s>>>(x, n->act[0], npix);
     for (int L = 0; L < NL; ++L) {
-        Conv c = conv_of(n, L, B);
+        TcConv c = n->tc[L];
+        c.ntiles = (long long)B * c.nty * c.ntx * c.nph;
+        c.bias = n->p + n->boff[L];
+        c.skip = n->skip[L] >= 0 ? n->act[n->skip[L]] : nullptr;
+        c.out = n->act[L + 1];
+        c.out32 = nullptr;
         if (L == NL - 1) {
             c.out = nullptr;
             c.out32 = n->y;
             c.out32_ch = TSURR_COUT;
         }
-        const long long tiles = cdiv((long long)B * c.hout * c.wout, TC_M);
-        const unsigned grid = (unsigned)std::min<long long>(tiles, n->num_sms);    // one CTA per SM
-        k_conv_fwd_tc<<<grid, TC_THREADS, tc_smem_bytes(c.cout), n->s>>>(c, n->err);
+        const unsigned grid = (unsigned)std::min<long long>(c.ntiles, n->num_sms);    // one CTA per SM
+        k_conv_fwd_tc<<<grid, TC_THREADS, tc_smem_bytes(c.N, c.cw), n->s>>>(n->tmA[L], n->tmB[L], c, n->err);
     }
     SCU(cudaGetLastError());
     return TSIM_OK;
