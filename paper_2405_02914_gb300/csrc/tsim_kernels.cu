@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
     const bool moves = MODE == MODE_COMMIT;
     const bool cands = MODE != MODE_ITER;
     const int count = min(d.cnt[par][b], CAP);          // an overflowed block was latched as an error
-    if (count == 0 && !cands) return;
+    if (count == 0) return;                             // no particles: no P2G, no moves, no candidate
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
