@@ -258,8 +258,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t row = 2u * (uint32_t)cw, stage_bytes = tc_stage_bytes(N, cw);
     const uint32_t a_slot = tc_a_slot(cw), b_slot = tc_b_slot(N, cw), b_base = (uint32_t)(64 / cw) * a_slot;
     const uint32_t a_box = (uint32_t)(c.bw * c.bh) * row, b_box = (uint32_t)N * row;
-    const int NS = tc_stages(N, cw), per_tap = c.cin / cw, kslices = cw / 16, cps = 64 / cw;
-    const int nchunks = 9 * per_tap;
+    const int NS = tc_stages(N, cw), kslices = cw / 16, cps = 64 / cw;
+    const int nchunks = 9 * (c.cin / cw);
     // stages 1024-byte aligned; then full[16], empty[16], accf[2], acce[2], the TMEM address
     const uint32_t raw = (uint32_t)__cvta_generic_to_shared(tc_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            uint32_t g = 0;                                // k-tiles loaded so far (ring position)
+            uint32_t s = 0, lap = 0;                       // ring slot and completed laps of the ring
             for (long long tile = blockIdx.x; tile < c.ntiles && ok; tile += gridDim.x) {
                 long long rest = tile;
                 const int ph = (int)(rest % c.nph);
@@ -303,19 +303,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int ty = (int)(rest % c.nty);
                 const int b = (int)(rest / c.nty);
                 const int X0 = tx * c.bw, Y0 = ty * c.bh, pa = ph >> 1, pb = ph & 1;
-                for (int kt = 0; kt < c.nkt; ++kt, ++g) {
-                    const uint32_t s = g % NS;
-                    // the stage was last read by the UMMAs of ring position g - NS
-                    if (g >= (uint32_t)NS && !bar_wait(empty + 8 * s, ((g / NS) - 1) & 1)) {
+                int ky = 0, kx = 0, ci = 0, left = nchunks;   // next chunk: tap (ky, kx), channels ci ..
+                for (int kt = 0; kt < c.nkt; ++kt) {
+                    // the stage was last read by the UMMAs of the previous lap
+                    if (lap > 0 && !bar_wait(empty + 8 * s, (lap - 1) & 1)) {
                         ok = false;
                         break;
                     }
-                    const int nq = min(cps, nchunks - kt * cps);     // chunks in this stage
+                    const int nq = min(cps, left);            // chunks in this stage
+                    left -= nq;
                     bar_expect_tx(full + 8 * s, (uint32_t)nq * (a_box + b_box));
                     const uint32_t sa = base + s * stage_bytes, sb = sa + b_base;
                     for (int q = 0; q < nq; ++q) {
-                        const int ch = kt * cps + q;
-                        const int tap = ch / per_tap, ci = (ch - tap * per_tap) * cw, ky = tap / 3, kx = tap - 3 * ky;
                         int x, y;
                         if (c.up) {
                             x = X0 + ((pb + kx + 1) >> 1) - 1;
@@ -325,7 +324,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             y = c.stride * Y0 + ky - 1;
                         }
                         tma_load_4d(sa + q * a_slot, &tmA, ci, x, y, b, full + 8 * s);
-                        tma_load_2d(sb + q * b_slot, &tmB, tap * c.cin + ci, 0, full + 8 * s);
+                        tma_load_2d(sb + q * b_slot, &tmB, (3 * ky + kx) * c.cin + ci, 0, full + 8 * s);
+                        ci += cw;
+                        if (ci == c.cin) {
+                            ci = 0;
+                            if (++kx == 3) {
+                                kx = 0;
+                                ++ky;
+                            }
+                        }
+                    }
+                    if (++s == (uint32_t)NS) {
+                        s = 0;
+                        ++lap;
                     }
                 }
             }
@@ -333,7 +344,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = umma_idesc(TC_M, N);
-            uint32_t g = 0;
+            uint32_t s = 0, lap = 0;
             int it = 0;
             for (long long tile = blockIdx.x; tile < c.ntiles && ok; tile += gridDim.x, ++it) {
                 const int b = it & 1;
@@ -344,20 +355,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * N);
-                for (int kt = 0; kt < c.nkt; ++kt, ++g) {
-                    const uint32_t s = g % NS;
-                    if (!bar_wait(full + 8 * s, (g / NS) & 1)) {
+                int left = nchunks;
+                for (int kt = 0; kt < c.nkt; ++kt) {
+                    if (!bar_wait(full + 8 * s, lap & 1)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     const uint32_t sa = base + s * stage_bytes, sb = sa + b_base;
-                    const int nq = min(cps, nchunks - kt * cps);
+                    const int nq = min(cps, left);
+                    left -= nq;
                     for (int q = 0; q < nq; ++q)
                         for (int j = 0; j < kslices; ++j)
                             umma_bf16(d, umma_desc_sw(sa + q * a_slot + 32 * j, row),
                                       umma_desc_sw(sb + q * b_slot + 32 * j, row), idesc, (kt | q | j) != 0);
                     umma_commit(empty + 8 * s);
+                    if (++s == (uint32_t)NS) {
+                        s = 0;
+                        ++lap;
+                    }
                 }
                 umma_commit(accf + 8 * b);      // tracks every UMMA of the tile
             }
