@@ -201,6 +201,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 // 1024-byte boundary, the swizzle atom); a stage holds 64 / cw chunks, so
 // every stage carries K = 64; as many stages as fit in 220 KB.
 constexpr uint32_t TC_SMEM_MAX = 220u * 1024u;
+// layers with cout <= 64 keep their ring within 110 KB so that two CTAs (two
+// pipelines and epilogues) share an SM
+__host__ __device__ inline uint32_t tc_smem_budget(int cout) { return cout <= 64 ? 110u * 1024u : TC_SMEM_MAX; }
 __host__ __device__ inline uint32_t tc_a_slot(int cw) { return (uint32_t)TC_M * 2u * (uint32_t)cw; }
 __host__ __device__ inline uint32_t tc_b_slot(int cout, int cw)
 {
@@ -212,7 +215,7 @@ __host__ __device__ inline uint32_t tc_stage_bytes(int cout, int cw)
 }
 __host__ __device__ inline int tc_stages(int cout, int cw)
 {
-    const int s = (int)((TC_SMEM_MAX - 2048u) / tc_stage_bytes(cout, cw));
+    const int s = (int)((tc_smem_budget(cout) - 2048u) / tc_stage_bytes(cout, cw));
     return s < 3 ? 3 : (s > TC_MAX_STAGES ? TC_MAX_STAGES : s);
 }
 __host__ __device__ inline uint32_t tc_smem_bytes(int cout, int cw)
@@ -384,12 +387,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         int it = 0;
         for (long long tile = blockIdx.x; tile < c.ntiles && ok; tile += gridDim.x, ++it) {
             const int b = it & 1;
-            // warp-uniform decision: tcgen05.ld below must be executed by all 32 lanes
-            if (!__all_sync(0xffffffffu, bar_wait(accf + 8 * b, (it >> 1) & 1))) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
             long long rest = tile;
             const int ph = (int)(rest % c.nph);
             rest /= c.nph;
@@ -402,17 +399,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const bool valid = r < c.bw * c.bh && gx < c.gw && gy < c.gh;
             const int oy = c.up ? 2 * gy + (ph >> 1) : gy, ox = c.up ? 2 * gx + (ph & 1) : gx;
             const long long pix = ((long long)bimg * c.hout + oy) * c.wout + ox;
+            // the skip values of the first 16 channels are requested before the
+            // wait for the accumulator, those of chunk c0 + 16 before chunk c0 is used
+            const uint4 *sp = c.skip && valid ? reinterpret_cast<const uint4 *>(c.skip + pix * N) : nullptr;
+            uint4 s_next[2] = {make_uint4(0u, 0u, 0u, 0u), make_uint4(0u, 0u, 0u, 0u)};
+            if (sp) {
+                s_next[0] = sp[0];
+                s_next[1] = sp[1];
+            }
+            // warp-uniform decision: tcgen05.ld below must be executed by all 32 lanes
+            if (!__all_sync(0xffffffffu, bar_wait(accf + 8 * b, (it >> 1) & 1))) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
             for (int c0 = 0; c0 < N; c0 += 16) {
                 uint32_t rr[16];
                 tmem_ld16(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(b * N + c0), rr);
+                const uint4 s_cur[2] = {s_next[0], s_next[1]};
+                if (sp && c0 + 16 < N) {
+                    s_next[0] = sp[(c0 + 16) / 8];
+                    s_next[1] = sp[(c0 + 16) / 8 + 1];
+                }
                 if (!valid) continue;
                 float v[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(rr[j]) + c.bias[c0 + j];
-                if (c.skip) {
-                    const uint4 *sp = reinterpret_cast<const uint4 *>(c.skip + pix * N + c0);
-                    uint4 s2[2] = {sp[0], sp[1]};
-                    const bf16 *se = reinterpret_cast<const bf16 *>(s2);
+                if (sp) {
+                    const bf16 *se = reinterpret_cast<const bf16 *>(s_cur);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) v[j] += bf2f(se[j]);
                 }
@@ -988,7 +1002,8 @@ static int run_forward(tsurr_net *n, const float *x, int B)
             c.out32 = n->y;
             c.out32_ch = TSURR_COUT;
         }
-        const unsigned grid = (unsigned)std::min<long long>(c.ntiles, n->num_sms);    // one CTA per SM
+        const int per_sm = c.N <= 64 ? 2 : 1;                                          // see tc_smem_budget
+        const unsigned grid = (unsigned)std::min<long long>(c.ntiles, (long long)per_sm * n->num_sms);
         k_conv_fwd_tc<<<grid, TC_THREADS, tc_smem_bytes(c.N, c.cw), n->s>>>(n->tmA[L], n->tmB[L], c, n->err);
     }
     SCU(cudaGetLastError());
