@@ -411,7 +411,11 @@ def test_autotune_advances_like_step_and_keeps_a_candidate(graph):
     scenes = [I.scene_small(cx=16, cy=12, cz=4, press=0.1e-3, n_press=300, slip=0.1e-3, n_slip=300, seed=1),
               I.scene_small(cx=8, cy=8, cz=4, press=0.08e-3, n_press=300, slip=0.05e-3, n_slip=300, mu=0.3,
                             seed=2),
-              I.scene_small(cx=24, cy=20, cz=6, press=0.12e-3, n_press=300, rotate=0.1, n_rot=300, seed=3)]
+              I.scene_small(cx=24, cy=20, cz=6, press=0.12e-3, n_press=300, slip=0.08e-3, n_slip=300, mu=0.4,
+                            seed=3)]
+    # (no sticking rotation here: two runs are not bit-identical -- grid atomics
+    # flush in any order -- and a sticking rotation amplifies that through the
+    # relative-rest decisions beyond the position tolerance)
     n = 600 if graph else 48
     states = [_init(sc) for sc in scenes]
     a = T.Sim(scenes, use_graph=graph, states=states)
