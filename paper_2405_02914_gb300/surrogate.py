@@ -8,7 +8,9 @@
   frame.  The frames stay on the device.
 * ``features``: the network input of a set of frames, x[B,H,W,12] =
   [heightmap, pixel x, pixel y, press depth, slip x, slip y, rotation,
-  E, nu, mu, tip x, tip y] (lengths in mm, scalars broadcast).
+  E, nu, mu, press rate, tangential rate] (lengths in mm, scalars
+  broadcast; the rates carry the loading speed, on which the dynamic part of
+  the simulated response depends).
 * ``train``: Adam on the masked displacement loss with the residual
   indicator channel (include/tsurr.h), all in the library's kernels.
 * ``evaluate`` / ``serve``: per-frame error against the IMPM frames,
@@ -63,17 +65,25 @@ def trajectory_state(kf: np.ndarray, k: float):
     return row[:3], row[3]
 
 
+RATE_LEVER = 3e-3      # rotation rate enters the tangential rate as the speed at 3 mm from the axis
+
+
 def frame_scalars(scene: I.Scene, k: int) -> np.ndarray:
-    """[press depth, slip x, slip y, rotation, E, nu, mu, tip x, tip y] at substep k,
-    normalised (lengths in mm, material constants centred on their ranges)."""
+    """[press depth, slip x, slip y, rotation, E, nu, mu, press rate, tangential
+    rate] at substep k, normalised: lengths in mm, material constants centred
+    on their ranges, rates in mm per 1000 substeps over the substep ending at k
+    (the tangential rate adds the slip speed and the rotation speed at
+    RATE_LEVER from the axis)."""
     tip, yaw = trajectory_state(scene.keyframes, k)
     tip0, yaw0 = trajectory_state(scene.keyframes, 0)
-    L = scene.gel.cx * scene.gel.dx
+    tipp, yawp = trajectory_state(scene.keyframes, k - 1)
     press = max(0.0, scene.gel.height - tip[2])
     m = scene.mat
+    press_rate = (tipp[2] - tip[2]) / MM * 1e3
+    tang_rate = (float(np.hypot(tip[0] - tipp[0], tip[1] - tipp[1])) + abs(yaw - yawp) * RATE_LEVER) / MM * 1e3
     return np.array([press / MM, (tip[0] - tip0[0]) / MM, (tip[1] - tip0[1]) / MM, yaw - yaw0,
                      (m.E - 1.9e5) / 1e5, (m.nu - 0.44) / 0.04, (scene.ind.mu - 0.6) / 0.4,
-                     (tip[0] - L / 2) / MM, (tip[1] - L / 2) / MM], np.float32)
+                     press_rate, tang_rate], np.float32)
 
 
 @dataclasses.dataclass
