@@ -137,6 +137,20 @@ def cpu_baseline(scene, max_seconds=15.0):
                       "serial, %.1f s" % (done, passes, x.shape[0], el)}
 
 
+def aggregate_ranks(ms, e2e_s, updates, e2e_updates, world, device):
+    """Whole-job figures of the replicas: the slowest rank's times (max) and
+    the work of all ranks (sum); world = 1 returns the inputs."""
+    if world <= 1:
+        return ms, e2e_s, updates, e2e_updates
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([ms, e2e_s], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    uu = torch.tensor([updates, e2e_updates], device=device, dtype=torch.float64)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return float(tt[0]), float(tt[1]), float(uu[0]), float(uu[1])
+
+
 def run_reference(args, scene):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -358,15 +372,7 @@ def main():
     e2e_updates = s3.particle_updates - s2.particle_updates
     T.tsim_destroy(ctx)
 
-    # max over ranks of the time, sum of the work
-    t_max, tot_updates, e2e_max, e2e_tot = ms, updates, e2e_s, e2e_updates
-    if world > 1:
-        tt = torch.tensor([ms, e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        uu = torch.tensor([updates, e2e_updates], device=dev, dtype=torch.float64)
-        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
-        t_max, e2e_max = float(tt[0]), float(tt[1])
-        tot_updates, e2e_tot = float(uu[0]), float(uu[1])
+    t_max, e2e_max, tot_updates, e2e_tot = aggregate_ranks(ms, e2e_s, updates, e2e_updates, world, dev)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
