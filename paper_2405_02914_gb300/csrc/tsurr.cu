@@ -218,9 +218,12 @@ __host__ __device__ inline int tc_stages(int cout, int cw)
     const int s = (int)((tc_smem_budget(cout) - 2048u) / tc_stage_bytes(cout, cw));
     return s < 3 ? 3 : (s > TC_MAX_STAGES ? TC_MAX_STAGES : s);
 }
+// + 1024 alignment slack + full/empty barriers (16 x 16) + accumulator
+// barriers and the TMEM address (64) + the packed tap tables (4 phases x 36
+// taps x 4 bytes + ntap[4] = 592), rounded up
 __host__ __device__ inline uint32_t tc_smem_bytes(int cout, int cw)
 {
-    return (uint32_t)tc_stages(cout, cw) * tc_stage_bytes(cout, cw) + 1024 + 16 * TC_MAX_STAGES + 64;
+    return (uint32_t)tc_stages(cout, cw) * tc_stage_bytes(cout, cw) + 1024 + 16 * TC_MAX_STAGES + 64 + 640;
 }
 // TMEM columns for two accumulators of n columns (a power of two >= 32)
 __host__ __device__ inline uint32_t tc_tmem_cols(int n)
@@ -459,62 +462,214 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 // ---------------------------------------------------------------- data gradient
 
-// dst[b][iy][ix][ci] += sum over (ky, kx, co) of W[co][ky][kx][ci] * dpre[b][oy][ox][co]
-// over the logical input (before any nearest pooling back to the physical input).
-__global__ void __launch_bounds__(GT) k_conv_dgrad(Conv c, const bf16 *dpre, float *dst)
+constexpr int TC_MAX_TAPS = 36;
+
+// The data gradient of a layer as a convolution-like contraction on the
+// tensor cores: acc32[pixel][n] += sum over taps t and channels c of
+// W^T[n][t][c] * dY[sample(pixel, t)][c].  Pixels are tiled by bw x bh
+// rectangles of a gh x gw grid (per image); with nph = 4 the grid is split
+// into output phases (a, b), and grid point (gy, gx) of phase (a, b) is
+// pixel (pm gy + a, pm gx + b).  Tap t of phase ph reads dY at (s_in Y0 +
+// tdy, s_in X0 + tdx) + s_in (row, column) of the tile (the tensor map
+// samples every s_in-th pixel) and the weights of tap tw (3 ky + kx).
+struct TcGrad {
+    int N, cin, cw;                // output channels (UMMA N), input channels, channels per chunk
+    int s_in, pm;                  // input sampling stride, output stride of the phase grid
+    int gw, gh;                    // tile grid
+    int bw, bh, ntx, nty, nph;     // tile rectangle, tiles per image row/column, phases (1 or 4)
+    const uint32_t *taps;          // device: 4 x TC_MAX_TAPS packed taps (dy + 128) | (dx + 128) << 8 | w << 16,
+                                   // then ntap[4]
+    long long ntiles;
+    int hout, wout;                // output tensor size
+    float *acc32;                  // [B][hout][wout][N] FP32, accumulated into (+=)
+};
+
+
+// Persistent, warp-specialised: each CTA walks output tiles (tile =
+// blockIdx.x, += gridDim.x).  The TMA thread fills a ring of stages, one
+// expect_tx arrival per stage on full[s]; the UMMA thread waits on full[s],
+// issues the stage's UMMAs into accumulator (tile & 1) and commits them to
+// empty[s] (which the TMA thread waits on before refilling the stage) and, at
+// the end of a tile, to accf[b].  The epilogue warps drain accumulator b with
+// tcgen05.ld while the next tile accumulates into the other, then release it
+// on acce[b].  Every wait is bounded; a wait that gives up sets *err.  The
+// pipeline is that of k_conv_fwd_tc with the taps read from the tables and a
+// per-phase tap count; the forward keeps its own kernel (computed taps), which
+// measured about 6% faster than this one on the forward layers.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_conv_dgrad_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcGrad c,
+                    int *err)
 {
-    __shared__ __align__(16) bf16 As[BM][BK];
-    __shared__ __align__(16) bf16 Bs[BN][BK];
-    const int M = c.B * c.hl * c.wl, N = c.cin, K = 9 * c.cout;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, wm = warp & 1, wn = warp >> 1;
-    const int lr = t >> 1, lh = t & 1;
-    const int m = m0 + lr, n = n0 + lr;
-    const bool mv = m < M, nv = n < N;
-    int bb = 0, iy = 0, ix = 0;
-    if (mv) { ix = m % c.wl; iy = (m / c.wl) % c.hl; bb = m / (c.wl * c.hl); }
-    auto load = [&](int kt, uint4 &va, uint4 &vb) {
-        const int kk = kt / c.cout, co = kt % c.cout + lh * 8, ky = kk / 3, kx = kk % 3;
-        va = make_uint4(0u, 0u, 0u, 0u);
-        vb = make_uint4(0u, 0u, 0u, 0u);
-        if (mv) {
-            const int ny = iy + 1 - ky, nx = ix + 1 - kx;
-            if (ny >= 0 && nx >= 0 && ny % c.stride == 0 && nx % c.stride == 0) {
-                const int oy = ny / c.stride, ox = nx / c.stride;
-                if (oy < c.hout && ox < c.wout)
-                    va = *reinterpret_cast<const uint4 *>(dpre + (((size_t)bb * c.hout + oy) * c.wout + ox) * c.cout +
-                                                          co);
+    extern __shared__ unsigned char tc_raw[];
+    const int N = c.N, cw = c.cw;
+    const uint32_t row = 2u * (uint32_t)cw, stage_bytes = tc_stage_bytes(N, cw);
+    const uint32_t a_slot = tc_a_slot(cw), b_slot = tc_b_slot(N, cw), b_base = (uint32_t)(64 / cw) * a_slot;
+    const uint32_t a_box = (uint32_t)(c.bw * c.bh) * row, b_box = (uint32_t)N * row;
+    const int NS = tc_stages(N, cw), kslices = cw / 16, cps = 64 / cw, per_tap = c.cin / cw;
+    // stages 1024-byte aligned; then full[16], empty[16], accf[2], acce[2], the TMEM address
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(tc_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t full = base + NS * stage_bytes, empty = full + 8 * TC_MAX_STAGES;
+    const uint32_t accf = empty + 8 * TC_MAX_STAGES, acce = accf + 16, tslot = acce + 16;
+    const uint32_t *tslot_p = reinterpret_cast<const uint32_t *>(tc_raw + (tslot - raw));
+    // tap tables in shared memory: (dy + 128) | (dx + 128) << 8 | w << 16 per tap, then ntap[4]
+    uint32_t *taps_s = reinterpret_cast<uint32_t *>(tc_raw + (tslot + 64 - raw));
+    int *ntap_s = reinterpret_cast<int *>(taps_s + 4 * TC_MAX_TAPS);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const uint32_t ncols = tc_tmem_cols(N);
+
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = t; i < 4 * TC_MAX_TAPS + 4; i += TC_THREADS) taps_s[i] = c.taps[i];
+    if (t == 0) {
+        for (int s = 0; s < NS; ++s) {
+            bar_init_n(full + 8 * s, 1);
+            bar_init_n(empty + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init_n(accf + 8 * b, 1);
+            bar_init_n(acce + 8 * b, 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot_p;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t s = 0, lap = 0;                       // ring slot and completed laps of the ring
+            for (long long tile = blockIdx.x; tile < c.ntiles && ok; tile += gridDim.x) {
+                long long rest = tile;
+                const int ph = (int)(rest % c.nph);
+                rest /= c.nph;
+                const int tx = (int)(rest % c.ntx);
+                rest /= c.ntx;
+                const int ty = (int)(rest % c.nty);
+                const int b = (int)(rest / c.nty);
+                const int X0 = c.s_in * tx * c.bw, Y0 = c.s_in * ty * c.bh;
+                const int nch = ntap_s[ph] * per_tap, nkt = (nch + cps - 1) / cps;
+                const uint32_t *tp = taps_s + ph * TC_MAX_TAPS;
+                int ti = 0, ci = 0, left = nch;                // next chunk: tap ti, channels ci ..
+                for (int kt = 0; kt < nkt; ++kt) {
+                    // the stage was last read by the UMMAs of the previous lap
+                    if (lap > 0 && !bar_wait(empty + 8 * s, (lap - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    const int nq = min(cps, left);            // chunks in this stage
+                    left -= nq;
+                    bar_expect_tx(full + 8 * s, (uint32_t)nq * (a_box + b_box));
+                    const uint32_t sa = base + s * stage_bytes, sb = sa + b_base;
+                    for (int q = 0; q < nq; ++q) {
+                        const uint32_t e = tp[ti];
+                        const int x = X0 + (int)((e >> 8) & 255u) - 128, y = Y0 + (int)(e & 255u) - 128;
+                        tma_load_4d(sa + q * a_slot, &tmA, ci, x, y, b, full + 8 * s);
+                        tma_load_2d(sb + q * b_slot, &tmB, (int)(e >> 16) * c.cin + ci, 0, full + 8 * s);
+                        ci += cw;
+                        if (ci == c.cin) {
+                            ci = 0;
+                            ++ti;
+                        }
+                    }
+                    if (++s == (uint32_t)NS) {
+                        s = 0;
+                        ++lap;
+                    }
+                }
             }
         }
-        if (nv) vb = *reinterpret_cast<const uint4 *>(c.wT + (size_t)n * K + kt + lh * 8);
-    };
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
-    uint4 va, vb;
-    load(0, va, vb);
-    for (int kt = 0; kt < K; kt += BK) {
-        *reinterpret_cast<uint4 *>(&As[lr][lh * 8]) = va;
-        *reinterpret_cast<uint4 *>(&Bs[lr][lh * 8]) = vb;
-        __syncthreads();
-        if (kt + BK < K) load(kt + BK, va, vb);
-        mma_tile<8>(reinterpret_cast<const uint32_t *>(As), reinterpret_cast<const uint32_t *>(Bs), acc, wm, wn,
-                    lane);
-        __syncthreads();
-    }
-    const int gid = lane >> 2, tig = lane & 3;
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int row = m0 + wm * 32 + mi * 16 + gid + (e >= 2 ? 8 : 0);
-                const int col = n0 + wn * 32 + ni * 8 + 2 * tig + (e & 1);
-                if (row < M && col < N) dst[(size_t)row * N + col] += acc[mi][ni][e];
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc(TC_M, N);
+            uint32_t s = 0, lap = 0;
+            int it = 0;
+            for (long long tile = blockIdx.x; tile < c.ntiles && ok; tile += gridDim.x, ++it) {
+                const int b = it & 1;
+                const int nch = ntap_s[(int)(tile % c.nph)] * per_tap, nkt = (nch + cps - 1) / cps;
+                // accumulator b was last drained by the epilogue of tile it - 2
+                if (it >= 2 && !bar_wait(acce + 8 * b, ((it >> 1) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * N);
+                int left = nch;
+                for (int kt = 0; kt < nkt; ++kt) {
+                    if (!bar_wait(full + 8 * s, lap & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = base + s * stage_bytes, sb = sa + b_base;
+                    const int nq = min(cps, left);
+                    left -= nq;
+                    for (int q = 0; q < nq; ++q)
+                        for (int j = 0; j < kslices; ++j)
+                            umma_bf16(d, umma_desc_sw(sa + q * a_slot + 32 * j, row),
+                                      umma_desc_sw(sb + q * b_slot + 32 * j, row), idesc, (kt | q | j) != 0);
+                    umma_commit(empty + 8 * s);
+                    if (++s == (uint32_t)NS) {
+                        s = 0;
+                        ++lap;
+                    }
+                }
+                umma_commit(accf + 8 * b);      // tracks every UMMA of the tile
             }
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows 32 (w % 4) .. + 31
+        const int e = warp & 3;
+        int it = 0;
+        for (long long tile = blockIdx.x; tile < c.ntiles && ok; tile += gridDim.x, ++it) {
+            const int b = it & 1;
+            long long rest = tile;
+            const int ph = (int)(rest % c.nph);
+            rest /= c.nph;
+            const int tx = (int)(rest % c.ntx);
+            rest /= c.ntx;
+            const int ty = (int)(rest % c.nty);
+            const int bimg = (int)(rest / c.nty);
+            const int r = e * 32 + lane;
+            const int gx = tx * c.bw + r % c.bw, gy = ty * c.bh + r / c.bw;
+            const bool valid = r < c.bw * c.bh && gx < c.gw && gy < c.gh;
+            const int oy = c.pm * gy + (ph >> 1), ox = c.pm * gx + (ph & 1);
+            const long long pix = ((long long)bimg * c.hout + oy) * c.wout + ox;
+            // warp-uniform decision: tcgen05.ld below must be executed by all 32 lanes
+            if (!__all_sync(0xffffffffu, bar_wait(accf + 8 * b, (it >> 1) & 1))) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            float4 *dp = reinterpret_cast<float4 *>(c.acc32 + pix * N);
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                uint32_t rr[16];
+                tmem_ld16(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(b * N + c0), rr);
+                if (!valid) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float4 a = dp[c0 / 4 + j];
+                    a.x += __uint_as_float(rr[4 * j]);
+                    a.y += __uint_as_float(rr[4 * j + 1]);
+                    a.z += __uint_as_float(rr[4 * j + 2]);
+                    a.w += __uint_as_float(rr[4 * j + 3]);
+                    dp[c0 / 4 + j] = a;
+                }
+            }
+            tc_fence_before();
+            bar_arrive(acce + 8 * b);
+        }
+    }
+    tc_fence_before();
+    const bool all_ok = __syncthreads_and(ok);
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    if (t == 0 && !all_ok) atomicOr(err, 1);
 }
 
 // ---------------------------------------------------------------- weight gradient
@@ -637,24 +792,6 @@ __global__ void k_dpre(const float *d, const bf16 *a, bf16 *dpre, float *skip_gr
     if (skip_grad) skip_grad[i] += g;
 }
 
-// gradient of a nearest x2 upsampling: sum the 2x2 children
-__global__ void k_pool2(const float *src, float *dst, int B, int h, int w, int ch)
-{
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n = (long long)B * h * w * ch;
-    if (i >= n) return;
-    const int c = (int)(i % ch);
-    const long long pix = i / ch;
-    const int x = (int)(pix % w), y = (int)((pix / w) % h), b = (int)(pix / ((long long)w * h));
-    float s = 0.f;
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx)
-            s += src[(((long long)b * 2 * h + 2 * y + dy) * 2 * w + 2 * x + dx) * ch + c];
-    dst[i] += s;
-}
-
 __global__ void k_bias_grad(const bf16 *dpre, long long npix, int ch, float *db)
 {
     const int c = threadIdx.x % ch;
@@ -710,7 +847,6 @@ struct tsurr_net {
     float *dact[NL + 1] = {};    // FP32 gradients of act[1..8]
     float *y = nullptr;          // FP32 network output [B][H][W][4]
     bf16 *dpre = nullptr;
-    float *dinl = nullptr;
     float *msum = nullptr;
     double *loss = nullptr;
     float *xbuf = nullptr, *tbuf = nullptr, *mbuf = nullptr;
@@ -718,6 +854,9 @@ struct tsurr_net {
     int num_sms = 1;
     CUtensorMap tmA[NL], tmB[NL];   // TMA maps of each layer's input (at max_batch) and BF16 weights
     TcConv tc[NL];                  // tile geometry of each layer's forward
+    CUtensorMap tmAd[NL], tmBd[NL]; // data gradient: maps of the layer's output gradient and transposed weights
+    TcGrad tcd[NL];                 // data gradient of each layer (L >= 1)
+    uint32_t *taps = nullptr;       // device copy of the data gradients' packed tap tables (NL tables)
     std::vector<void *> allocs;
 };
 
@@ -770,9 +909,78 @@ static Conv conv_of(const tsurr_net *n, int L, int B)
 }
 
 // TMA maps and tile geometry of the nine forward convolutions (once per net)
-static bool setup_forward(tsurr_net *n, std::string *why)
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+// tile geometry of an op on a gh x gw grid
+template <class C>
+static void tc_tiles(C &c, int gh, int gw)
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    c.gw = gw;
+    c.gh = gh;
+    c.bw = std::min(gw, TC_M);
+    c.bh = std::max(1, std::min(gh, TC_M / c.bw));
+    c.ntx = (gw + c.bw - 1) / c.bw;
+    c.nty = (gh + c.bh - 1) / c.bh;
+}
+
+// packed tap tables of every op, host copy (uploaded once per net)
+struct TapTable {
+    uint32_t e[4 * TC_MAX_TAPS + 4];
+};
+
+static void tc_tap(TapTable &tt, int ph, int dy, int dx, int w)
+{
+    uint32_t &n = tt.e[4 * TC_MAX_TAPS + ph];
+    tt.e[ph * TC_MAX_TAPS + n] = (uint32_t)(dy + 128) | ((uint32_t)(dx + 128) << 8) | ((uint32_t)w << 16);
+    ++n;
+}
+
+// TMA maps of an op: input NHWC [maxB][h][w][cin] sampled every es-th pixel
+// in boxes of cw channels x bw x bh samples, weights [N rows][9 cin]
+template <class C>
+static bool tc_maps(EncodeFn encode, const C &c, int es_, const void *in, int h, int w, int maxB, const void *wts,
+                    CUtensorMap *ma, CUtensorMap *mb, std::string *why)
+{
+    const cuuint32_t es = (cuuint32_t)es_;
+    const cuuint64_t gdim[4] = {(cuuint64_t)c.cin, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)maxB};
+    const cuuint64_t gstr[3] = {(cuuint64_t)c.cin * 2, (cuuint64_t)w * c.cin * 2, (cuuint64_t)h * w * c.cin * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)c.cw, (cuuint32_t)c.bw * es, (cuuint32_t)c.bh * es, 1};
+    const cuuint32_t estr[4] = {1, es, es, 1};
+    const CUtensorMapSwizzle swz = c.cw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                              : (c.cw == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+    CUresult r = encode(ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(in), gdim, gstr, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *why = "input tensor map: error " + std::to_string((int)r);
+        return false;
+    }
+    const cuuint64_t wdim[2] = {(cuuint64_t)9 * c.cin, (cuuint64_t)c.N};
+    const cuuint64_t wstr[1] = {(cuuint64_t)9 * c.cin * 2};
+    const cuuint32_t wbox[2] = {(cuuint32_t)c.cw, (cuuint32_t)c.N};
+    const cuuint32_t westr[2] = {1, 1};
+    r = encode(mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(wts), wdim, wstr, wbox, westr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *why = "weight tensor map: error " + std::to_string((int)r);
+        return false;
+    }
+    return true;
+}
+
+// Tap tables, tile geometry and TMA maps of the nine forward convolutions and
+// of the data gradients of layers 1..8 (once per net).
+//  forward, stride s:  out[y][x] = sum_t W[t] in[s y + ky - 1][s x + kx - 1]
+//  forward, up:        phase (a, b): low-res in[i + floor((a + ky - 1) / 2)][..]
+//  gradient, stride 1: dX[y][x] = sum_t W^T[t] dY[y + 1 - ky][x + 1 - kx]
+//  gradient, stride 2: phase (a, b) of dX: taps with (a + 1 - ky) even,
+//                      dY[i + (a + 1 - ky) / 2][..]
+//  gradient, up:       dX[i][j] = sum over the 2 x 2 upsampled children (a, b)
+//                      and the nine taps of W^T dY[2 i + a + 1 - ky][..]
+static bool setup_convs(tsurr_net *n, std::string *why)
+{
+    static EncodeFn encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
         void *fn = nullptr;
@@ -782,56 +990,91 @@ static bool setup_forward(tsurr_net *n, std::string *why)
             *why = "cuTensorMapEncodeTiled is not available";
             return false;
         }
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        encode = reinterpret_cast<EncodeFn>(fn);
     }
+    std::vector<TapTable> tabs(NL);
+    memset(tabs.data(), 0, tabs.size() * sizeof(TapTable));
+    const size_t TT = sizeof(TapTable) / sizeof(uint32_t);
     for (int L = 0; L < NL; ++L) {
+        const int hin = n->hin[L], win = n->win[L], cin = n->cin[L], cout = n->cout[L];
+        const int up = n->up[L], st = n->stride[L];
+        TapTable &tg = tabs[L];
+        const int hout = (up ? 2 * hin : hin) / st, wout = (up ? 2 * win : win) / st;
+        // forward: taps computed in the kernel from up / stride
         TcConv &c = n->tc[L];
         memset(&c, 0, sizeof(c));
-        const int hin = n->hin[L], win = n->win[L], cin = n->cin[L], cout = n->cout[L];
         c.N = cout;
         c.cin = cin;
         c.K = 9 * cin;
         c.cw = std::min(cin, 64);
         c.nkt = (9 * (cin / c.cw) + (64 / c.cw) - 1) / (64 / c.cw);
-        c.up = n->up[L];
-        c.stride = n->stride[L];
-        c.hout = (c.up ? 2 * hin : hin) / c.stride;
-        c.wout = (c.up ? 2 * win : win) / c.stride;
-        c.gw = c.up ? win : c.wout;
-        c.gh = c.up ? hin : c.hout;
-        c.bw = std::min(c.gw, TC_M);
-        c.bh = std::max(1, std::min(c.gh, TC_M / c.bw));
-        c.ntx = (c.gw + c.bw - 1) / c.bw;
-        c.nty = (c.gh + c.bh - 1) / c.bh;
-        c.nph = c.up ? 4 : 1;
+        c.up = up;
+        c.stride = st;
+        c.hout = hout;
+        c.wout = wout;
+        c.nph = up ? 4 : 1;
         c.relu = n->relu[L];
-        const cuuint32_t es = (cuuint32_t)(c.up ? 1 : c.stride);
-        const cuuint64_t gdim[4] = {(cuuint64_t)cin, (cuuint64_t)win, (cuuint64_t)hin, (cuuint64_t)n->maxB};
-        const cuuint64_t gstr[3] = {(cuuint64_t)cin * 2, (cuuint64_t)win * cin * 2, (cuuint64_t)hin * win * cin * 2};
-        const cuuint32_t box[4] = {(cuuint32_t)c.cw, (cuuint32_t)c.bw * es, (cuuint32_t)c.bh * es, 1};
-        const CUtensorMapSwizzle swz = c.cw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
-                                                  : (c.cw == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
-        const cuuint32_t estr[4] = {1, es, es, 1};
-        CUresult r = encode(&n->tmA[L], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)n->act[n->src[L]], gdim, gstr, box,
-                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            *why = "tensor map of layer " + std::to_string(L) + " input: error " + std::to_string((int)r);
+        if (up) tc_tiles(c, hin, win);
+        else tc_tiles(c, hout, wout);
+        std::string w2;
+        if (!tc_maps(encode, c, up ? 1 : st, n->act[n->src[L]], hin, win, n->maxB, n->wb[L], &n->tmA[L], &n->tmB[L],
+                     &w2)) {
+            *why = "layer " + std::to_string(L) + " forward " + w2;
             return false;
         }
-        const cuuint64_t wdim[2] = {(cuuint64_t)c.K, (cuuint64_t)cout};
-        const cuuint64_t wstr[1] = {(cuuint64_t)c.K * 2};
-        const cuuint32_t wbox[2] = {(cuuint32_t)c.cw, (cuuint32_t)cout};
-        const cuuint32_t westr[2] = {1, 1};
-        r = encode(&n->tmB[L], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)n->wb[L], wdim, wstr, wbox, westr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            *why = "tensor map of layer " + std::to_string(L) + " weights: error " + std::to_string((int)r);
+        if (L == 0) continue;          // no gradient towards the network input
+        // data gradient: input = the layer's output gradient (cout channels), N = cin
+        TcGrad &d = n->tcd[L];
+        memset(&d, 0, sizeof(d));
+        d.N = cin;
+        d.cin = cout;
+        d.cw = std::min(cout, 64);
+        d.hout = hin;
+        d.wout = win;
+        d.taps = n->taps + L * TT;
+        if (up) {
+            d.s_in = 2;
+            d.pm = 1;
+            d.nph = 1;
+            tc_tiles(d, hin, win);
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b)
+                    for (int t = 0; t < 9; ++t) tc_tap(tg, 0, a + 1 - t / 3, b + 1 - t % 3, t);
+        } else if (st == 2) {
+            d.s_in = 1;
+            d.pm = 2;
+            d.nph = 4;
+            tc_tiles(d, hout, wout);
+            for (int ph = 0; ph < 4; ++ph)
+                for (int t = 0; t < 9; ++t) {
+                    const int a = ph >> 1, b = ph & 1, ky = t / 3, kx = t % 3;
+                    if (((a + 1 - ky) & 1) == 0 && ((b + 1 - kx) & 1) == 0)
+                        tc_tap(tg, ph, (a + 1 - ky) / 2, (b + 1 - kx) / 2, t);
+                }
+        } else {
+            d.s_in = 1;
+            d.pm = 1;
+            d.nph = 1;
+            tc_tiles(d, hin, win);
+            for (int t = 0; t < 9; ++t) tc_tap(tg, 0, 1 - t / 3, 1 - t % 3, t);
+        }
+        if (!tc_maps(encode, d, d.s_in, n->dpre, hout, wout, n->maxB, n->wt[L], &n->tmAd[L], &n->tmBd[L], &w2)) {
+            *why = "layer " + std::to_string(L) + " gradient " + w2;
             return false;
         }
     }
+    if (cudaMemcpy(n->taps, tabs.data(), tabs.size() * sizeof(TapTable), cudaMemcpyHostToDevice) != cudaSuccess) {
+        *why = "upload of the tap tables failed";
+        return false;
+    }
     return true;
+}
+
+// persistent grid: every SM holds one CTA, two for N <= 64 (see tc_smem_budget)
+static unsigned tc_grid(const tsurr_net *n, int N, long long ntiles)
+{
+    const int per_sm = N <= 64 ? 2 : 1;
+    return (unsigned)std::min<long long>(ntiles, (long long)per_sm * n->num_sms);
 }
 
 extern "C" int tsurr_create(int max_batch, int height, int width, void *stream, tsurr_net **out)
@@ -892,19 +1135,12 @@ extern "C" int tsurr_create(int max_batch, int height, int width, void *stream, 
         if (ok && i >= 1) ok = alloc((void **)&n->dact[i], e * sizeof(float));
         if (i >= 1 && e > maxl) maxl = e;
     }
-    long long maxlogical = 0;
-    for (int L = 0; L < NL; ++L)
-        if (upv[L]) {
-            const long long e = (long long)max_batch * (2 * hi[L]) * (2 * hi[L] * W / H) * ci[L];
-            if (e > maxlogical) maxlogical = e;
-        }
     const long long npix = (long long)max_batch * H * W;
     ok = ok && alloc((void **)&n->y, npix * 4 * sizeof(float)) && alloc((void **)&n->dpre, maxl * sizeof(bf16)) &&
-         alloc((void **)&n->dinl, (maxlogical > 0 ? maxlogical : 1) * sizeof(float)) &&
          alloc((void **)&n->msum, 64) && alloc((void **)&n->loss, 64) &&
          alloc((void **)&n->xbuf, npix * TSURR_CIN * sizeof(float)) &&
          alloc((void **)&n->tbuf, npix * 3 * sizeof(float)) && alloc((void **)&n->mbuf, npix * sizeof(float)) &&
-         alloc((void **)&n->err, 64);
+         alloc((void **)&n->err, 64) && alloc((void **)&n->taps, NL * sizeof(TapTable));
     if (!ok) {
         cudaGetLastError();
         for (void *p : n->allocs) cudaFree(p);
@@ -923,13 +1159,15 @@ extern "C" int tsurr_create(int max_batch, int height, int width, void *stream, 
         n->num_sms = 1;
     if (cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(TC_SMEM_MAX + 2048)) !=
             cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_dgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(TC_SMEM_MAX + 2048)) != cudaSuccess ||
         cudaStreamSynchronize(n->s) != cudaSuccess) {
         for (void *p : n->allocs) cudaFree(p);
         delete n;
         return sfail(TSIM_ERR_CUDA, "tsurr_create: initialisation failed");
     }
     std::string why;
-    if (!setup_forward(n, &why)) {
+    if (!setup_convs(n, &why)) {
         for (void *p : n->allocs) cudaFree(p);
         delete n;
         return sfail(TSIM_ERR_CUDA, "tsurr_create: " + why);
@@ -1002,9 +1240,8 @@ static int run_forward(tsurr_net *n, const float *x, int B)
             c.out32 = n->y;
             c.out32_ch = TSURR_COUT;
         }
-        const int per_sm = c.N <= 64 ? 2 : 1;                                          // see tc_smem_budget
-        const unsigned grid = (unsigned)std::min<long long>(c.ntiles, (long long)per_sm * n->num_sms);
-        k_conv_fwd_tc<<<grid, TC_THREADS, tc_smem_bytes(c.N, c.cw), n->s>>>(n->tmA[L], n->tmB[L], c, n->err);
+        k_conv_fwd_tc<<<tc_grid(n, c.N, c.ntiles), TC_THREADS, tc_smem_bytes(c.N, c.cw), n->s>>>(n->tmA[L], n->tmB[L],
+                                                                                                  c, n->err);
     }
     SCU(cudaGetLastError());
     return TSIM_OK;
@@ -1086,17 +1323,14 @@ extern "C" int tsurr_backward(tsurr_net *n, const float *x, const float *target,
         dim3 gw(cdiv(c.cout, BM), cdiv(9LL * c.cin, BN), cdiv(P, pps));
         k_conv_wgrad<<<gw, GT, 0, n->s>>>(c, n->dpre, n->g + n->woff[L], pps);
         k_bias_grad<<<128, 256, 0, n->s>>>(n->dpre, P, c.cout, n->g + n->boff[L]);
-        // data gradient towards the layer input (not needed for the network input)
+        // data gradient towards the layer input (not needed for the network input), on the
+        // tensor cores, accumulated into the FP32 gradient of that activation
         if (L > 0) {
-            dim3 gd(cdiv((long long)B * c.hl * c.wl, BM), cdiv(c.cin, BN));
-            if (c.up) {
-                SCU(cudaMemsetAsync(n->dinl, 0, (size_t)B * c.hl * c.wl * c.cin * sizeof(float), n->s));
-                k_conv_dgrad<<<gd, GT, 0, n->s>>>(c, n->dpre, n->dinl);
-                const long long nin = (long long)B * c.hin * c.win * c.cin;
-                k_pool2<<<cdiv(nin, 256), 256, 0, n->s>>>(n->dinl, n->dact[L], B, c.hin, c.win, c.cin);
-            } else {
-                k_conv_dgrad<<<gd, GT, 0, n->s>>>(c, n->dpre, n->dact[L]);
-            }
+            TcGrad d = n->tcd[L];
+            d.ntiles = (long long)B * d.nty * d.ntx * d.nph;
+            d.acc32 = n->dact[L];
+            k_conv_dgrad_tc<<<tc_grid(n, d.N, d.ntiles), TC_THREADS, tc_smem_bytes(d.N, d.cw), n->s>>>(
+                n->tmAd[L], n->tmBd[L], d, n->err);
         }
     }
     SCU(cudaGetLastError());
