@@ -782,26 +782,60 @@ __global__ void k_loss(const float *y, const float *tgt, const float *mask, cons
 
 // gradient at a layer output -> gradient before the ReLU (BF16 for the GEMMs),
 // also added to the gradient of the skip source when the layer has one
-__global__ void k_dpre(const float *d, const bf16 *a, bf16 *dpre, float *skip_grad, long long n, int relu)
+// eight elements per thread (n8 = elements / 8; every layer's channel count is a multiple of 8)
+__global__ void k_dpre(const float *d, const bf16 *a, bf16 *dpre, float *skip_grad, long long n8, int relu)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float g = d[i];
-    if (relu && !(bf2f(a[i]) > 0.f)) g = 0.f;
-    dpre[i] = f2bf(g);
-    if (skip_grad) skip_grad[i] += g;
+    if (i >= n8) return;
+    const float4 d0 = reinterpret_cast<const float4 *>(d)[2 * i], d1 = reinterpret_cast<const float4 *>(d)[2 * i + 1];
+    float g[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+    const uint4 av = reinterpret_cast<const uint4 *>(a)[i];
+    const bf16 *ae = reinterpret_cast<const bf16 *>(&av);
+    uint4 ov;
+    bf16 *oe = reinterpret_cast<bf16 *>(&ov);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (relu && !(bf2f(ae[j]) > 0.f)) g[j] = 0.f;
+        oe[j] = f2bf(g[j]);
+    }
+    reinterpret_cast<uint4 *>(dpre)[i] = ov;
+    if (skip_grad) {
+        float4 *sp = reinterpret_cast<float4 *>(skip_grad) + 2 * i;
+        float4 s0 = sp[0], s1 = sp[1];
+        s0.x += g[0]; s0.y += g[1]; s0.z += g[2]; s0.w += g[3];
+        s1.x += g[4]; s1.y += g[5]; s1.z += g[6]; s1.w += g[7];
+        sp[0] = s0;
+        sp[1] = s1;
+    }
 }
 
-__global__ void k_bias_grad(const bf16 *dpre, long long npix, int ch, float *db)
+// db[c] += sum over pixels of dpre[p][c].  Each thread sums one group of
+// eight channels (a 16-byte load) over a strided set of pixels: the grid
+// stride is a multiple of 256 and ch / 8 divides 256, so a thread keeps its
+// group.  The block adds its threads' partial sums in shared memory and
+// issues one atomic per channel.
+constexpr int BG_THREADS = 256;
+__global__ void __launch_bounds__(BG_THREADS) k_bias_grad(const bf16 *dpre, long long npix, int ch, float *db)
 {
-    const int c = threadIdx.x % ch;
-    const int lanes_per = blockDim.x / ch;
-    const int sub = threadIdx.x / ch;
-    if (sub >= lanes_per) return;
-    float s = 0.f;
-    for (long long p = (long long)blockIdx.x * lanes_per + sub; p < npix; p += (long long)gridDim.x * lanes_per)
-        s += bf2f(dpre[p * ch + c]);
-    atomicAdd(db + c, s);
+    __shared__ float part[BG_THREADS * 8];
+    const int groups = ch / 8;
+    const long long nvec = npix * groups;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (long long v = (long long)blockIdx.x * BG_THREADS + threadIdx.x; v < nvec; v += (long long)gridDim.x * BG_THREADS) {
+        const uint4 u = reinterpret_cast<const uint4 *>(dpre)[v];
+        const bf16 *e = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] += bf2f(e[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) part[threadIdx.x * 8 + j] = s[j];
+    __syncthreads();
+    for (int c = threadIdx.x; c < ch; c += BG_THREADS) {
+        float t = 0.f;
+        for (int k = c / 8; k < BG_THREADS; k += groups) t += part[k * 8 + c % 8];
+        atomicAdd(db + c, t);
+    }
 }
 
 __global__ void k_adam(float *p, const float *g, float *m1, float *m2, long long n, float lr, float b1, float b2,
@@ -1313,7 +1347,7 @@ extern "C" int tsurr_backward(tsurr_net *n, const float *x, const float *target,
         const long long nout = (long long)B * c.hout * c.wout * c.cout;
         if (L < NL - 1) {
             float *skipg = n->skip[L] >= 0 ? n->dact[n->skip[L]] : nullptr;
-            k_dpre<<<cdiv(nout, 256), 256, 0, n->s>>>(n->dact[L + 1], n->act[L + 1], n->dpre, skipg, nout, 1);
+            k_dpre<<<cdiv(nout / 8, 256), 256, 0, n->s>>>(n->dact[L + 1], n->act[L + 1], n->dpre, skipg, nout / 8, 1);
         }
         // weight and bias gradients
         const long long P = (long long)B * c.hout * c.wout;
@@ -1322,7 +1356,10 @@ extern "C" int tsurr_backward(tsurr_net *n, const float *x, const float *target,
         pps = (pps + BK - 1) / BK * BK;
         dim3 gw(cdiv(c.cout, BM), cdiv(9LL * c.cin, BN), cdiv(P, pps));
         k_conv_wgrad<<<gw, GT, 0, n->s>>>(c, n->dpre, n->g + n->woff[L], pps);
-        k_bias_grad<<<128, 256, 0, n->s>>>(n->dpre, P, c.cout, n->g + n->boff[L]);
+        const long long nvec = P * (c.cout / 8);
+        const unsigned bg = (unsigned)std::max<long long>(1, std::min<long long>(cdiv(nvec, 8LL * BG_THREADS),
+                                                                                  4LL * n->num_sms));
+        k_bias_grad<<<bg, BG_THREADS, 0, n->s>>>(n->dpre, P, c.cout, n->g + n->boff[L]);
         // data gradient towards the layer input (not needed for the network input), on the
         // tensor cores, accumulated into the FP32 gradient of that activation
         if (L > 0) {
