@@ -87,12 +87,13 @@ struct Conv {
 // implicit GEMMs, D[pixels][cout] = A[pixels][9 cin] B[cout][9 cin]^T, with
 // UMMA M = 128 pixels, N = cout, K = 16 per instruction and the accumulator in
 // tensor memory (TMEM).  Both operands are fetched by TMA tensor copies that
-// land directly in the UMMA no-swizzle K-major layout (8-row x 16-byte core
-// matrices): the A tile of one 8-channel chunk of one tap is a 4-D box
-// {8 channels, bw x bh pixels, 1 image} of the NHWC input at the tap's offset
-// (zero fill outside the image = the convolution's zero padding; stride-2
-// layers sample every other pixel through the tensor map's element strides),
-// the B tile a 2-D box {8 k, cout rows} of the weights.  An output tile is a
+// land directly in the swizzled K-major layout the UMMA descriptors name
+// (rows of 32, 64 or 128 bytes, 8-row swizzle atoms): the A tile of one chunk
+// of cw = min(cin, 64) channels of one tap is a 4-D box {cw channels, bw x bh
+// pixels, 1 image} of the NHWC input at the tap's offset (zero fill outside
+// the image = the convolution's zero padding; stride-2 layers sample every
+// other pixel through the tensor map's element strides), the B tile a 2-D box
+// {cw k, cout rows} of the weights.  An output tile is a
 // bw x bh rectangle of one image (bw * bh <= 128 rows of M).  Layers that read
 // a nearest x2 upsampling of their input are split into the four output
 // phases (2i + a, 2j + b): for a phase, tap (ky, kx) reads low-resolution
@@ -672,12 +673,253 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (t == 0 && !all_ok) atomicOr(err, 1);
 }
 
-// ---------------------------------------------------------------- weight gradient
+// ---------------------------------------------------------------- weight gradient on tcgen05
+
+// dW[co][ky][kx][ci] = sum over output pixels p of dY[p][co] X(p, ky, kx)[ci],
+// where X(p, ky, kx) is the layer's input at the tap's position, is a GEMM
+// with the pixels as K: D[co][ci] = A[co][p] B[ci][p]^T for each tap.  Both
+// operands are made K-major by writing them channel-major first:
+//   dYT[co][b][y][x]           the output gradient, transposed;
+//   G[kx][ci][b][r][x]         the input, transposed, with the tap's column
+//                              offset (and the layer's column sampling:
+//                              stride 2, or the nearest x2 upsampling)
+//                              applied, one copy per kx;
+// so that an output row segment of kw pixels is one TMA box of either operand
+// ({kw pixels, 1 row, 1 image, channels}: kw * 2 bytes per channel row, the
+// swizzle span) and the tap's row offset is the box's row coordinate:
+// r = y + ky - 1 (stride 1), 2 y + ky - 1 (stride 2), (y + ky - 1) >> 1
+// (upsampled input; rows outside the image read as zeros).  kw = 64, 32 or
+// 16 (the output width must be a multiple of 16).
+
+// G[k][c][b][r][xo] = src[b][r][xs(xo, k)][c] (zero where xs leaves the
+// image), k < nk; mode 0: xs = xo + k - off, mode 1: xs = 2 xo + k - off,
+// mode 2: u = xo + k - off inside [0, wout), xs = u >> 1.  Eight consecutive
+// xo per thread (one 16-byte store); the channel runs fastest across threads
+// so that the loads of a warp are contiguous.  b runs over the batch B, the
+// layout keeps maxB images.
+__global__ void k_wg_gather(const bf16 *__restrict__ src, bf16 *__restrict__ dst, int B, int maxB, int rows,
+                            int win, int wout, int ch, int nk, int off, int mode)
+{
+    const int ng = wout / 8;
+    const long long total = (long long)nk * B * rows * ng * ch;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % ch);
+        long long rest = i / ch;
+        const int xg = (int)(rest % ng);
+        rest /= ng;
+        const int r = (int)(rest % rows);
+        rest /= rows;
+        const int b = (int)(rest % B);
+        const int k = (int)(rest / B);
+        uint4 ov;
+        bf16 *oe = reinterpret_cast<bf16 *>(&ov);
+        const bf16 *srow = src + ((long long)b * rows + r) * win * ch + c;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int xo = xg * 8 + j;
+            int xs;
+            bool in;
+            if (mode == 2) {
+                const int u = xo + k - off;
+                in = u >= 0 && u < wout;
+                xs = u >> 1;
+            } else {
+                xs = (mode == 1 ? 2 * xo : xo) + k - off;
+                in = xs >= 0 && xs < win;
+            }
+            bf16 v = __float2bfloat16(0.f);
+            if (in) v = srow[(long long)xs * ch];
+            oe[j] = v;
+        }
+        *reinterpret_cast<uint4 *>(dst + ((((long long)k * ch + c) * maxB + b) * rows + r) * wout + xg * 8) = ov;
+    }
+}
+
+struct TcWgrad {
+    int N, co, kw, nseg;           // UMMA N = ci, output channels, pixels per chunk, chunks per output row
+    int hout, mode;                // output rows; row offset rule: 0 stride 1, 1 stride 2, 2 upsampled input
+    int mblocks, arows;            // 128-row blocks of co, rows of the A box (min(co, 128))
+    long long nchunks;             // chunks of the batch (B * hout * nseg)
+    int cpsplit, splits;           // chunks per split, splits
+    long long nunits;              // 9 taps x mblocks x splits
+    float *dw;                     // the layer's weight gradient [co][9][ci], accumulated into (FP32 atomics)
+};
+
+// Same pipeline as k_conv_fwd_tc (TMA thread, UMMA thread, four epilogue
+// warps, double-buffered TMEM accumulator); a work unit is (tap, 128-row
+// block of co, split of the pixel chunks), ordered so that the nine taps of
+// a split run side by side and share its output-gradient boxes in L2.  The
+// epilogue adds the unit's D[co][ci] to dW with vector FP32 atomics.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcWgrad c,
+                    int *err)
+{
+    extern __shared__ unsigned char tc_raw[];
+    const int N = c.N, kw = c.kw;
+    const uint32_t row = 2u * (uint32_t)kw, stage_bytes = tc_stage_bytes(N, kw);
+    const uint32_t a_slot = tc_a_slot(kw), b_slot = tc_b_slot(N, kw), b_base = (uint32_t)(64 / kw) * a_slot;
+    const uint32_t a_box = (uint32_t)c.arows * row, b_box = (uint32_t)N * row;
+    const int NS = tc_stages(N, kw), kslices = kw / 16, cps = 64 / kw;
+    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(tc_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t full = base + NS * stage_bytes, empty = full + 8 * TC_MAX_STAGES;
+    const uint32_t accf = empty + 8 * TC_MAX_STAGES, acce = accf + 16, tslot = acce + 16;
+    const uint32_t *tslot_p = reinterpret_cast<const uint32_t *>(tc_raw + (tslot - raw));
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const uint32_t ncols = tc_tmem_cols(N);
+
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot), "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        for (int s = 0; s < NS; ++s) {
+            bar_init_n(full + 8 * s, 1);
+            bar_init_n(empty + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init_n(accf + 8 * b, 1);
+            bar_init_n(acce + 8 * b, 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot_p;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t s = 0, lap = 0;
+            for (long long u = blockIdx.x; u < c.nunits && ok; u += gridDim.x) {
+                const int tap = (int)(u % 9);
+                const long long rest = u / 9;
+                const int mb = (int)(rest % c.mblocks);
+                const int sp = (int)(rest / c.mblocks);
+                const int ky = tap / 3, kx = tap - 3 * ky;
+                const long long c0 = (long long)sp * c.cpsplit;
+                const int n = (int)min((long long)c.cpsplit, c.nchunks - c0);
+                const int nkt = (n + cps - 1) / cps;
+                // first chunk: output row segment seg of row y of image b
+                int seg = (int)(c0 % c.nseg);
+                const long long ry0 = c0 / c.nseg;
+                int y = (int)(ry0 % c.hout), b = (int)(ry0 / c.hout);
+                int left = n;
+                for (int kt = 0; kt < nkt; ++kt) {
+                    if (lap > 0 && !bar_wait(empty + 8 * s, (lap - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    const int nq = min(cps, left);
+                    left -= nq;
+                    bar_expect_tx(full + 8 * s, (uint32_t)nq * (a_box + b_box));
+                    const uint32_t sa = base + s * stage_bytes, sb = sa + b_base;
+                    for (int q = 0; q < nq; ++q) {
+                        const int yr = c.mode == 1 ? 2 * y + ky - 1 : (c.mode == 2 ? (y + ky - 1) >> 1 : y + ky - 1);
+                        tma_load_4d(sa + q * a_slot, &tmA, seg * kw, y, b, mb * 128, full + 8 * s);
+                        tma_load_4d(sb + q * b_slot, &tmB, seg * kw, yr, b, kx * N, full + 8 * s);
+                        if (++seg == c.nseg) {
+                            seg = 0;
+                            if (++y == c.hout) {
+                                y = 0;
+                                ++b;
+                            }
+                        }
+                    }
+                    if (++s == (uint32_t)NS) {
+                        s = 0;
+                        ++lap;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc(TC_M, N);
+            uint32_t s = 0, lap = 0;
+            int it = 0;
+            for (long long u = blockIdx.x; u < c.nunits && ok; u += gridDim.x, ++it) {
+                const int b = it & 1;
+                const long long rest = u / 9;
+                const int sp = (int)(rest / c.mblocks);
+                const int n = (int)min((long long)c.cpsplit, c.nchunks - (long long)sp * c.cpsplit);
+                const int nkt = (n + cps - 1) / cps;
+                if (it >= 2 && !bar_wait(acce + 8 * b, ((it >> 1) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * N);
+                int left = n;
+                for (int kt = 0; kt < nkt; ++kt) {
+                    if (!bar_wait(full + 8 * s, lap & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = base + s * stage_bytes, sb = sa + b_base;
+                    const int nq = min(cps, left);
+                    left -= nq;
+                    for (int q = 0; q < nq; ++q)
+                        for (int j = 0; j < kslices; ++j)
+                            umma_bf16(d, umma_desc_sw(sa + q * a_slot + 32 * j, row),
+                                      umma_desc_sw(sb + q * b_slot + 32 * j, row), idesc, (kt | q | j) != 0);
+                    umma_commit(empty + 8 * s);
+                    if (++s == (uint32_t)NS) {
+                        s = 0;
+                        ++lap;
+                    }
+                }
+                umma_commit(accf + 8 * b);
+            }
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = rows of co
+        const int e = warp & 3;
+        int it = 0;
+        for (long long u = blockIdx.x; u < c.nunits && ok; u += gridDim.x, ++it) {
+            const int b = it & 1;
+            const int tap = (int)(u % 9);
+            const int mb = (int)((u / 9) % c.mblocks);
+            const int co = mb * 128 + e * 32 + lane;
+            const bool valid = co < c.co;
+            if (!__all_sync(0xffffffffu, bar_wait(accf + 8 * b, (it >> 1) & 1))) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            float4 *dp = reinterpret_cast<float4 *>(c.dw + ((long long)co * 9 + tap) * N);
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                uint32_t rr[16];
+                tmem_ld16(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(b * N + c0), rr);
+                if (!valid) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    atomicAdd(dp + c0 / 4 + j, make_float4(__uint_as_float(rr[4 * j]), __uint_as_float(rr[4 * j + 1]),
+                                                           __uint_as_float(rr[4 * j + 2]),
+                                                           __uint_as_float(rr[4 * j + 3])));
+            }
+            tc_fence_before();
+            bar_arrive(acce + 8 * b);
+        }
+    }
+    tc_fence_before();
+    const bool all_ok = __syncthreads_and(ok);
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    if (t == 0 && !all_ok) atomicOr(err, 1);
+}
+
+// ---------------------------------------------------------------- weight gradient (narrow layers)
 
 constexpr int WS = 9;   // row stride (32-bit words) of the transposed tiles: 18 BF16
 
 // dW[co][ky][kx][ci] += sum over output pixels of dpre[p][co] * in_logical[p shifted][ci];
-// split over pixel ranges (blockIdx.z), FP32 atomics into dW.
+// split over pixel ranges (blockIdx.z), FP32 atomics into dW.  Used for the
+// layers whose output width is not a multiple of 16 (small frames).
 __global__ void __launch_bounds__(GT) k_conv_wgrad(Conv c, const bf16 *dpre, float *dW, int pix_per_split)
 {
     __shared__ __align__(16) bf16 As[BM * 2 * WS];
@@ -891,6 +1133,11 @@ struct tsurr_net {
     CUtensorMap tmAd[NL], tmBd[NL]; // data gradient: maps of the layer's output gradient and transposed weights
     TcGrad tcd[NL];                 // data gradient of each layer (L >= 1)
     uint32_t *taps = nullptr;       // device copy of the data gradients' packed tap tables (NL tables)
+    bool wg_tc[NL] = {};            // weight gradient on tcgen05 (output width a multiple of 16)
+    CUtensorMap tmAw[NL], tmBw[NL]; // weight gradient: maps of dYT and G
+    TcWgrad tcw[NL];
+    bf16 *dyt = nullptr;            // output gradient, channel-major [co][maxB][hout][wout]
+    bf16 *gx = nullptr;             // layer input, channel-major with column offsets [3][ci][maxB][rows][wout]
     std::vector<void *> allocs;
 };
 
@@ -1101,7 +1348,73 @@ static bool setup_convs(tsurr_net *n, std::string *why)
         *why = "upload of the tap tables failed";
         return false;
     }
+    // weight gradients on tcgen05: maps of dYT {wout, hout, maxB, co} and
+    // G {wout, rows, maxB, 3 ci}, boxes of one row segment of kw pixels
+    for (int L = 0; L < NL; ++L) {
+        if (!n->wg_tc[L]) continue;
+        const int up = n->up[L], st = n->stride[L], ci = n->cin[L], co = n->cout[L];
+        const int hout = (up ? 2 * n->hin[L] : n->hin[L]) / st, wout = (up ? 2 * n->win[L] : n->win[L]) / st;
+        const int rows = n->hin[L];
+        TcWgrad &w = n->tcw[L];
+        memset(&w, 0, sizeof(w));
+        w.N = ci;
+        w.co = co;
+        w.kw = wout % 64 == 0 ? 64 : (wout % 32 == 0 ? 32 : 16);
+        w.nseg = wout / w.kw;
+        w.hout = hout;
+        w.mode = up ? 2 : (st == 2 ? 1 : 0);
+        w.mblocks = (co + TC_M - 1) / TC_M;
+        w.arows = std::min(co, TC_M);
+        const CUtensorMapSwizzle swz = w.kw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                                  : (w.kw == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        const cuuint64_t adim[4] = {(cuuint64_t)wout, (cuuint64_t)hout, (cuuint64_t)n->maxB, (cuuint64_t)co};
+        const cuuint64_t astr[3] = {(cuuint64_t)wout * 2, (cuuint64_t)hout * wout * 2,
+                                    (cuuint64_t)n->maxB * hout * wout * 2};
+        const cuuint32_t abox[4] = {(cuuint32_t)w.kw, 1, 1, (cuuint32_t)w.arows};
+        CUresult r = encode(&n->tmAw[L], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)n->dyt, adim, astr, abox, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        const cuuint64_t bdim[4] = {(cuuint64_t)wout, (cuuint64_t)rows, (cuuint64_t)n->maxB, (cuuint64_t)3 * ci};
+        const cuuint64_t bstr[3] = {(cuuint64_t)wout * 2, (cuuint64_t)rows * wout * 2,
+                                    (cuuint64_t)n->maxB * rows * wout * 2};
+        const cuuint32_t bbox[4] = {(cuuint32_t)w.kw, 1, 1, (cuuint32_t)ci};
+        if (r == CUDA_SUCCESS)
+            r = encode(&n->tmBw[L], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)n->gx, bdim, bstr, bbox, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            *why = "layer " + std::to_string(L) + " weight-gradient tensor map: error " + std::to_string((int)r);
+            return false;
+        }
+    }
     return true;
+}
+
+// weight gradient of layer L on tcgen05 for a batch of B: channel-major
+// copies of the output gradient and of the input, then the contraction
+static void launch_wgrad_tc(tsurr_net *n, int L, int B)
+{
+    TcWgrad w = n->tcw[L];
+    const int up = n->up[L], st = n->stride[L], ci = n->cin[L], co = n->cout[L];
+    const int wout = w.nseg * w.kw, rows = n->hin[L];
+    const unsigned gmax = (unsigned)(8 * n->num_sms);
+    const long long ty = (long long)B * w.hout * (wout / 8) * co;
+    k_wg_gather<<<std::min(cdiv(ty, 256), gmax), 256, 0, n->s>>>(n->dpre, n->dyt, B, n->maxB, w.hout, wout, wout, co,
+                                                                  1, 0, 0);
+    const long long tg = 3LL * B * rows * (wout / 8) * ci;
+    k_wg_gather<<<std::min(cdiv(tg, 256), gmax), 256, 0, n->s>>>(n->act[n->src[L]], n->gx, B, n->maxB, rows,
+                                                                  n->win[L], wout, ci, 3, 1, up ? 2 : (st == 2 ? 1 : 0));
+    const int cps = 64 / w.kw;
+    const int per_sm = ci <= 64 ? 2 : 1;                                        // see tc_smem_budget
+    w.nchunks = (long long)B * w.hout * w.nseg;
+    const long long want = std::max<long long>(1, (2LL * per_sm * n->num_sms + 9 * w.mblocks - 1) / (9 * w.mblocks));
+    w.cpsplit = (int)std::max<long long>(8LL * cps, (w.nchunks + want - 1) / want);
+    w.splits = (int)((w.nchunks + w.cpsplit - 1) / w.cpsplit);
+    w.nunits = 9LL * w.mblocks * w.splits;
+    w.dw = n->g + n->woff[L];
+    const unsigned grid = (unsigned)std::min<long long>(w.nunits, (long long)per_sm * n->num_sms);
+    k_conv_wgrad_tc<<<grid, TC_THREADS, tc_smem_bytes(ci, w.kw), n->s>>>(n->tmAw[L], n->tmBw[L], w, n->err);
 }
 
 // persistent grid: every SM holds one CTA, two for N <= 64 (see tc_smem_budget)
@@ -1175,6 +1488,16 @@ extern "C" int tsurr_create(int max_batch, int height, int width, void *stream, 
          alloc((void **)&n->xbuf, npix * TSURR_CIN * sizeof(float)) &&
          alloc((void **)&n->tbuf, npix * 3 * sizeof(float)) && alloc((void **)&n->mbuf, npix * sizeof(float)) &&
          alloc((void **)&n->err, 64) && alloc((void **)&n->taps, NL * sizeof(TapTable));
+    // channel-major operands of the tcgen05 weight gradients (layers whose
+    // output width is a multiple of 16)
+    long long gmax = 0;
+    for (int L = 0; L < NL; ++L) {
+        const int wout = (upv[L] ? 2 * n->win[L] : n->win[L]) / st[L];
+        n->wg_tc[L] = wout % 16 == 0;
+        if (n->wg_tc[L]) gmax = std::max(gmax, 3LL * ci[L] * max_batch * hi[L] * wout);
+    }
+    ok = ok && alloc((void **)&n->dyt, maxl * sizeof(bf16)) &&
+         alloc((void **)&n->gx, std::max<long long>(gmax, 8) * sizeof(bf16));
     if (!ok) {
         cudaGetLastError();
         for (void *p : n->allocs) cudaFree(p);
@@ -1194,6 +1517,8 @@ extern "C" int tsurr_create(int max_batch, int height, int width, void *stream, 
     if (cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(TC_SMEM_MAX + 2048)) !=
             cudaSuccess ||
         cudaFuncSetAttribute(k_conv_dgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(TC_SMEM_MAX + 2048)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(TC_SMEM_MAX + 2048)) != cudaSuccess ||
         cudaStreamSynchronize(n->s) != cudaSuccess) {
         for (void *p : n->allocs) cudaFree(p);
@@ -1351,11 +1676,15 @@ extern "C" int tsurr_backward(tsurr_net *n, const float *x, const float *target,
         }
         // weight and bias gradients
         const long long P = (long long)B * c.hout * c.wout;
-        const int splits = (int)std::max<long long>(1, std::min<long long>(256, P / 2048));
-        int pps = (int)((P + splits - 1) / splits);
-        pps = (pps + BK - 1) / BK * BK;
-        dim3 gw(cdiv(c.cout, BM), cdiv(9LL * c.cin, BN), cdiv(P, pps));
-        k_conv_wgrad<<<gw, GT, 0, n->s>>>(c, n->dpre, n->g + n->woff[L], pps);
+        if (n->wg_tc[L]) {
+            launch_wgrad_tc(n, L, B);
+        } else {
+            const int splits = (int)std::max<long long>(1, std::min<long long>(256, P / 2048));
+            int pps = (int)((P + splits - 1) / splits);
+            pps = (pps + BK - 1) / BK * BK;
+            dim3 gw(cdiv(c.cout, BM), cdiv(9LL * c.cin, BN), cdiv(P, pps));
+            k_conv_wgrad<<<gw, GT, 0, n->s>>>(c, n->dpre, n->g + n->woff[L], pps);
+        }
         const long long nvec = P * (c.cout / 8);
         const unsigned bg = (unsigned)std::max<long long>(1, std::min<long long>(cdiv(nvec, 8LL * BG_THREADS),
                                                                                   4LL * n->num_sms));

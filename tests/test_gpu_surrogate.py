@@ -56,7 +56,10 @@ def test_forward_matches_oracle(B, H, W):
     assert np.abs(y - y16).max() <= 3e-2 * np.abs(y16).max()
 
 
-@pytest.mark.parametrize("B,H,W", [(2, 16, 16), (3, 16, 24), (1, 32, 8)])
+# (2, 16, 16), (3, 16, 24), (1, 32, 8): weight gradients of the narrow layers
+# on mma.sync; (2, 32, 48): layers 0, 7, 8 on tcgen05 with three 16-pixel
+# row segments per output row; (1, 128, 128): every layer on tcgen05
+@pytest.mark.parametrize("B,H,W", [(2, 16, 16), (3, 16, 24), (1, 32, 8), (2, 32, 48), (1, 128, 128)])
 def test_backward_matches_oracle(B, H, W):
     p = I.surrogate_params(21, bias_std=0.1, scale_last=1.0)
     x, t, m = I.surrogate_batch(22, B, H, W)
