@@ -30,10 +30,12 @@
  * Conventions as in tsim.h: int status codes (TSIM_*), tsim_last_error()
  * for the reason, the caller's stream, no allocation after tsurr_create.
  *
- * Kernels: the forward convolutions and the data-gradient convolutions run
- * on the tcgen05 tensor cores (UMMA M = 128 pixels x N = cout, or N = cin
- * for the data gradient, accumulators in tensor memory); the weight-gradient
- * convolutions on mma.sync m16n8k16.
+ * Kernels: the forward, data-gradient and weight-gradient convolutions run
+ * on the tcgen05 tensor cores (accumulators in tensor memory; UMMA M = 128
+ * pixels x N = cout forward, N = cin for the data gradient, M = cout x
+ * N = cin over the pixels for the weight gradient); the weight gradient of
+ * a layer whose output width is not a multiple of 16 runs on mma.sync
+ * m16n8k16.
  */
 #ifndef TSURR_H
 #define TSURR_H
