@@ -737,9 +737,10 @@ __global__ void k_wg_gather(const bf16 *__restrict__ src, bf16 *__restrict__ dst
 }
 
 struct TcWgrad {
-    int N, co, kw, nseg;           // UMMA N = ci, output channels, pixels per chunk, chunks per output row
+    int N, ci, co, kw, nseg;       // UMMA N, input and output channels, pixels per chunk, chunks per output row
+    int swap;                      // 0: M = co (A = dYT), N = ci (B = G); 1: M = ci (A = G), N = co (B = dYT)
     int hout, mode;                // output rows; row offset rule: 0 stride 1, 1 stride 2, 2 upsampled input
-    int mblocks, arows;            // 128-row blocks of co, rows of the A box (min(co, 128))
+    int mdim, mblocks, arows;      // M-side channels, their 128-row blocks, rows of the A box (min(mdim, 128))
     long long nchunks;             // chunks of the batch (B * hout * nseg)
     int cpsplit, splits;           // chunks per split, splits
     long long nunits;              // 9 taps x mblocks x splits
@@ -750,7 +751,10 @@ struct TcWgrad {
 // warps, double-buffered TMEM accumulator); a work unit is (tap, 128-row
 // block of co, split of the pixel chunks), ordered so that the nine taps of
 // a split run side by side and share its output-gradient boxes in L2.  The
-// epilogue adds the unit's D[co][ci] to dW with vector FP32 atomics.
+// epilogue adds the unit's D to dW with FP32 atomics: D[co][ci] (vectors of
+// four ci) or, with the operands swapped for thin layers (cout < cin, cout <
+// 128, so that fewer of the 128 M rows are padding), D[ci][co] (one ci per
+// lane, coalesced across the warp).
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcWgrad c,
                     int *err)
@@ -819,8 +823,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint32_t sa = base + s * stage_bytes, sb = sa + b_base;
                     for (int q = 0; q < nq; ++q) {
                         const int yr = c.mode == 1 ? 2 * y + ky - 1 : (c.mode == 2 ? (y + ky - 1) >> 1 : y + ky - 1);
-                        tma_load_4d(sa + q * a_slot, &tmA, seg * kw, y, b, mb * 128, full + 8 * s);
-                        tma_load_4d(sb + q * b_slot, &tmB, seg * kw, yr, b, kx * N, full + 8 * s);
+                        if (c.swap) {
+                            tma_load_4d(sa + q * a_slot, &tmA, seg * kw, yr, b, kx * c.ci + mb * 128, full + 8 * s);
+                            tma_load_4d(sb + q * b_slot, &tmB, seg * kw, y, b, 0, full + 8 * s);
+                        } else {
+                            tma_load_4d(sa + q * a_slot, &tmA, seg * kw, y, b, mb * 128, full + 8 * s);
+                            tma_load_4d(sb + q * b_slot, &tmB, seg * kw, yr, b, kx * c.ci, full + 8 * s);
+                        }
                         if (++seg == c.nseg) {
                             seg = 0;
                             if (++y == c.hout) {
@@ -877,30 +886,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
     } else {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = rows of co
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = rows of the M side
         const int e = warp & 3;
         int it = 0;
         for (long long u = blockIdx.x; u < c.nunits && ok; u += gridDim.x, ++it) {
             const int b = it & 1;
             const int tap = (int)(u % 9);
             const int mb = (int)((u / 9) % c.mblocks);
-            const int co = mb * 128 + e * 32 + lane;
-            const bool valid = co < c.co;
+            const int m = mb * 128 + e * 32 + lane;      // co, or ci when swapped
+            const bool valid = m < c.mdim;
             if (!__all_sync(0xffffffffu, bar_wait(accf + 8 * b, (it >> 1) & 1))) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            float4 *dp = reinterpret_cast<float4 *>(c.dw + ((long long)co * 9 + tap) * N);
             for (int c0 = 0; c0 < N; c0 += 16) {
                 uint32_t rr[16];
                 tmem_ld16(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)(b * N + c0), rr);
                 if (!valid) continue;
+                if (c.swap) {
+                    // column n = co: dW[co][tap][m]
+                    float *dp = c.dw + (long long)tap * c.ci + m;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    atomicAdd(dp + c0 / 4 + j, make_float4(__uint_as_float(rr[4 * j]), __uint_as_float(rr[4 * j + 1]),
-                                                           __uint_as_float(rr[4 * j + 2]),
-                                                           __uint_as_float(rr[4 * j + 3])));
+                    for (int j = 0; j < 16; ++j) atomicAdd(dp + (long long)(c0 + j) * 9 * c.ci, __uint_as_float(rr[j]));
+                } else {
+                    float4 *dp = reinterpret_cast<float4 *>(c.dw + ((long long)m * 9 + tap) * c.ci + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        atomicAdd(dp + j, make_float4(__uint_as_float(rr[4 * j]), __uint_as_float(rr[4 * j + 1]),
+                                                      __uint_as_float(rr[4 * j + 2]), __uint_as_float(rr[4 * j + 3])));
+                }
             }
             tc_fence_before();
             bar_arrive(acce + 8 * b);
@@ -1357,31 +1372,36 @@ static bool setup_convs(tsurr_net *n, std::string *why)
         const int rows = n->hin[L];
         TcWgrad &w = n->tcw[L];
         memset(&w, 0, sizeof(w));
-        w.N = ci;
+        w.swap = co < TC_M && ci > co;
+        w.N = w.swap ? co : ci;
+        w.ci = ci;
         w.co = co;
+        w.mdim = w.swap ? ci : co;
         w.kw = wout % 64 == 0 ? 64 : (wout % 32 == 0 ? 32 : 16);
         w.nseg = wout / w.kw;
         w.hout = hout;
         w.mode = up ? 2 : (st == 2 ? 1 : 0);
-        w.mblocks = (co + TC_M - 1) / TC_M;
-        w.arows = std::min(co, TC_M);
+        w.mblocks = (w.mdim + TC_M - 1) / TC_M;
+        w.arows = std::min(w.mdim, TC_M);
         const CUtensorMapSwizzle swz = w.kw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
                                                   : (w.kw == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
         const cuuint32_t estr[4] = {1, 1, 1, 1};
         const cuuint64_t adim[4] = {(cuuint64_t)wout, (cuuint64_t)hout, (cuuint64_t)n->maxB, (cuuint64_t)co};
         const cuuint64_t astr[3] = {(cuuint64_t)wout * 2, (cuuint64_t)hout * wout * 2,
                                     (cuuint64_t)n->maxB * hout * wout * 2};
-        const cuuint32_t abox[4] = {(cuuint32_t)w.kw, 1, 1, (cuuint32_t)w.arows};
-        CUresult r = encode(&n->tmAw[L], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)n->dyt, adim, astr, abox, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        // dYT with boxes of min(co, 128) rows (A) or co rows (B); G with boxes
+        // of ci rows (B) or min(ci, 128) rows (A)
+        const cuuint32_t ybox[4] = {(cuuint32_t)w.kw, 1, 1, (cuuint32_t)(w.swap ? co : w.arows)};
+        CUresult r = encode(w.swap ? &n->tmBw[L] : &n->tmAw[L], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)n->dyt,
+                            adim, astr, ybox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         const cuuint64_t bdim[4] = {(cuuint64_t)wout, (cuuint64_t)rows, (cuuint64_t)n->maxB, (cuuint64_t)3 * ci};
         const cuuint64_t bstr[3] = {(cuuint64_t)wout * 2, (cuuint64_t)rows * wout * 2,
                                     (cuuint64_t)n->maxB * rows * wout * 2};
-        const cuuint32_t bbox[4] = {(cuuint32_t)w.kw, 1, 1, (cuuint32_t)ci};
+        const cuuint32_t gbox[4] = {(cuuint32_t)w.kw, 1, 1, (cuuint32_t)(w.swap ? w.arows : ci)};
         if (r == CUDA_SUCCESS)
-            r = encode(&n->tmBw[L], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)n->gx, bdim, bstr, bbox, estr,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            r = encode(w.swap ? &n->tmAw[L] : &n->tmBw[L], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)n->gx, bdim,
+                       bstr, gbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             *why = "layer " + std::to_string(L) + " weight-gradient tensor map: error " + std::to_string((int)r);
@@ -1406,7 +1426,7 @@ static void launch_wgrad_tc(tsurr_net *n, int L, int B)
     k_wg_gather<<<std::min(cdiv(tg, 256), gmax), 256, 0, n->s>>>(n->act[n->src[L]], n->gx, B, n->maxB, rows,
                                                                   n->win[L], wout, ci, 3, 1, up ? 2 : (st == 2 ? 1 : 0));
     const int cps = 64 / w.kw;
-    const int per_sm = ci <= 64 ? 2 : 1;                                        // see tc_smem_budget
+    const int per_sm = w.N <= 64 ? 2 : 1;                                       // see tc_smem_budget
     w.nchunks = (long long)B * w.hout * w.nseg;
     const long long want = std::max<long long>(1, (2LL * per_sm * n->num_sms + 9 * w.mblocks - 1) / (9 * w.mblocks));
     w.cpsplit = (int)std::max<long long>(8LL * cps, (w.nchunks + want - 1) / want);
@@ -1414,7 +1434,7 @@ static void launch_wgrad_tc(tsurr_net *n, int L, int B)
     w.nunits = 9LL * w.mblocks * w.splits;
     w.dw = n->g + n->woff[L];
     const unsigned grid = (unsigned)std::min<long long>(w.nunits, (long long)per_sm * n->num_sms);
-    k_conv_wgrad_tc<<<grid, TC_THREADS, tc_smem_bytes(ci, w.kw), n->s>>>(n->tmAw[L], n->tmBw[L], w, n->err);
+    k_conv_wgrad_tc<<<grid, TC_THREADS, tc_smem_bytes(w.N, w.kw), n->s>>>(n->tmAw[L], n->tmBw[L], w, n->err);
 }
 
 // persistent grid: every SM holds one CTA, two for N <= 64 (see tc_smem_budget)
