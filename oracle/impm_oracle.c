@@ -34,8 +34,13 @@
  * affine velocity fields; free fall in closed form; energy balance of a free
  * elastic oscillation; uniaxial compression against linear elasticity; SDF
  * surface points, eikonal property and gradients; contact projection
- * invariants; surface readout closed forms; keyframe interpolation.
- * Parity unpinned: long stick/slip trajectories (checked only against the
+ * invariants; surface readout closed forms; keyframe interpolation; the
+ * relative-rest loop (a pure press accepts every first pass; a sticking
+ * slip needs repeated passes); a sticking slip or turn drags the contact
+ * patch the indenter's way by less than the indenter moved, and without
+ * friction it stays in place.
+ * Partly unpinned: the exact lag of the gel behind a sticking indenter over
+ * long stick/slip trajectories has no closed form (checked against the
  * CUDA path).
  */
 #include <math.h>

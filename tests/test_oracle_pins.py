@@ -475,6 +475,59 @@ def test_frictionless_sphere_rotation_invariance():
     assert a.x[:, 2].min() < sc.gel.height - 0.3 * sc.gel.dx    # it did press
 
 
+def _drag_run(mu, slip=0.0, rotate=0.0, n_move=0):
+    """Press 0.4 mm in 60 substeps, then slip along +x or turn about the
+    vertical axis in n_move substeps; returns the top-layer particles within
+    the contact patch at the end of the press (before, after) and the tip."""
+    sc = I.scene_small(cx=12, cy=12, cz=4, n_press=60, slip=slip, n_slip=n_move if slip else 0, rotate=rotate,
+                       n_rot=n_move if rotate else 0, mu=mu, press=0.4e-3)
+    s = O.make_scene(sc)
+    ind = O.make_indenter(sc.ind)
+    st = _state(sc)
+    O.run(s, ind, sc.keyframes, 0, 60, st)
+    x1 = st.x.copy()
+    O.run(s, ind, sc.keyframes, 60, n_move, st)
+    tip = sc.keyframes[1, 1:3]
+    dx = sc.gel.dx
+    r = np.hypot(x1[:, 0] - tip[0], x1[:, 1] - tip[1])
+    return x1, st.x, tip, r, (x1[:, 2] > x1[:, 2].max() - dx), dx
+
+
+def test_sticking_slip_drags_the_contact_patch():
+    """Coulomb friction in the stick regime (relative rest, mu = 1) drags the
+    gel under the indenter along the slip direction, by less than the slip
+    itself (the elastic gel lags); without friction there is no tangential
+    traction and the patch stays nearly in place.  A wrong sign of the
+    object velocity or of the tangential projection, or friction that is not
+    applied, fails this."""
+    slip = 0.5e-3
+    out = {}
+    for mu in (1.0, 0.0):
+        x1, x2, tip, r, top, dx = _drag_run(mu, slip=slip, n_move=100)
+        patch = top & (r < 1.5 * dx)
+        assert patch.sum() >= 20
+        d = (x2 - x1)[patch]
+        out[mu] = d[:, 0].mean() / slip
+        assert abs(d[:, 1].mean()) < 0.02 * slip          # nothing across the slip direction
+    assert 0.2 < out[1.0] < 1.0, out
+    assert abs(out[0.0]) < 0.1, out
+
+
+@pytest.mark.parametrize("rotate", [0.3, -0.3])
+def test_sticking_rotation_turns_the_contact_patch(rotate):
+    """A sticking indenter that turns about its vertical axis by theta turns
+    the contact patch the same way (omega x r, counter-clockwise for theta >
+    0), by a fraction of theta.  The frictionless case is the rotation
+    invariance pin above."""
+    x1, x2, tip, r, top, dx = _drag_run(1.0, rotate=rotate, n_move=100)
+    ring = top & (r > 0.5 * dx) & (r < 2.0 * dx)
+    assert ring.sum() >= 40
+    a1 = np.arctan2(x1[ring, 1] - tip[1], x1[ring, 0] - tip[0])
+    a2 = np.arctan2(x2[ring, 1] - tip[1], x2[ring, 0] - tip[0])
+    turn = np.angle(np.exp(1j * (a2 - a1))).mean() / rotate
+    assert 0.1 < turn < 1.0, turn
+
+
 # ------------------------------------------------------------------ surface readout
 
 def test_surface_readout_closed_forms():
