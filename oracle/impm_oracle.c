@@ -34,7 +34,9 @@
  * affine velocity fields; free fall in closed form; energy balance of a free
  * elastic oscillation; uniaxial compression against linear elasticity; SDF
  * surface points, eikonal property and gradients; contact projection
- * invariants; surface readout closed forms; keyframe interpolation; the
+ * invariants; surface readout closed forms; the displacement splat (rigid
+ * translation, linear fields, untagged and unreached pixels); the sphere's
+ * underside height map; keyframe interpolation; the
  * relative-rest loop (a pure press accepts every first pass; a sticking
  * slip needs repeated passes); a sticking slip or turn drags the contact
  * patch the indenter's way by less than the indenter moved, and without

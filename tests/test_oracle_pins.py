@@ -557,3 +557,74 @@ def test_surface_readout_closed_forms():
     st.tag[:] = 0
     h3, n3 = O.surface(st, W, W, dx, 7.0)
     assert np.all(h3 == 7.0) and np.all(n3[..., 2] == 1.0)
+
+
+def _top_lattice(W, dx, z0=3e-3):
+    """Two particles per pixel and axis, symmetric about the pixel centres."""
+    u = (np.arange(2 * W) + 0.5) * dx / 2
+    X, Y = np.meshgrid(u, u, indexing="xy")
+    return np.stack([X.ravel(), Y.ravel(), np.full(X.size, z0)], 1)
+
+
+def test_surface_displacement_closed_forms():
+    """The displacement field is a normalised B-spline splat of x - x_ref at
+    the reference positions: a rigid translation comes back exactly
+    everywhere; a linear field u = A x_ref comes back as A times the pixel
+    centre on the interior pixels (the lattice is symmetric about them, so
+    the weighted mean reference position is the centre); untagged particles
+    are ignored and pixels out of every particle's reach read zero."""
+    dx, W = 0.5e-3, 10
+    xref = _top_lattice(W, dx)
+    n = xref.shape[0]
+    tag = np.full(n, I.TAG_TOP, dtype=np.uint32)
+    z = np.zeros((n, 9))
+
+    def disp(x, t, xr=xref, Wd=W):
+        return O.surface_disp(O.State(x, np.zeros_like(x), z[:len(x)], z[:len(x)], t), xr, Wd, Wd, dx)
+
+    u0 = np.array([3e-5, -2e-5, -7e-5])
+    u = disp(xref + u0, tag)
+    assert np.abs(u - u0).max() < 1e-18
+    A = np.array([[0.01, -0.03, 0.02], [0.04, 0.005, -0.01], [-0.02, 0.03, 0.015]])
+    u = disp(xref + xref @ A.T, tag)
+    Xc = (np.arange(W) + 0.5) * dx
+    ref = np.einsum("ij,yxj->yxi", A, np.stack(np.broadcast_arrays(Xc[None, :], Xc[:, None], 3e-3), -1))
+    inner = slice(1, W - 1)
+    assert np.abs(u[inner, inner] - ref[inner, inner]).max() < 1e-17
+    # untagged particles with a large displacement change nothing
+    t2 = tag.copy()
+    t2[::3] = 0
+    x2 = xref + u0
+    x2[::3] += 1e-3
+    xr2 = xref.copy()
+    u2 = disp(x2, t2)
+    assert np.abs(u2 - u0).max() < 1e-18
+    # particles only in the left two pixel columns: far pixels read zero
+    left = xr2[:, 0] < 2 * dx
+    u3 = O.surface_disp(O.State((xref + u0)[left], np.zeros((left.sum(), 3)), z[:left.sum()], z[:left.sum()],
+                                tag[left]), xref[left], W, W, dx)
+    assert np.all(u3[:, 4:] == 0.0) and np.abs(u3[:, :2] - u0).max() < 1e-18
+
+
+def test_indenter_height_of_a_sphere():
+    """The underside of a sphere of radius R centred at c above the pixel
+    column at distance rho from its axis lies at c_z - sqrt(R^2 - rho^2):
+    the height map reads that minus the gel top, +clip where the column
+    misses the sphere, clipped to [-clip, clip]; turning the sphere about
+    its axis changes nothing."""
+    Hgel, R, pitch, W, clip = 4e-3, 2e-3, 0.5e-3, 20, 3e-3
+    ind = O.make_indenter(I.sphere(R, 0.5))
+    tip = np.array([5.1e-3, 4.9e-3, Hgel - 0.2e-3])          # pressed 0.2 mm into the gel
+    for yaw in (0.0, 0.7):
+        kf = I.keyframes([(0, tip[0], tip[1], tip[2], yaw)])
+        ps = O.pose(kf, 0, 1e-5, R)
+        h = O.indenter_height(ind, ps, Hgel, W, W, pitch, clip, 0.05e-3)
+        xc = (np.arange(W) + 0.5) * pitch
+        rho2 = (xc[None, :] - kf[0, 1]) ** 2 + (xc[:, None] - kf[0, 2]) ** 2
+        inside = rho2 < R * R
+        ref = np.where(inside, kf[0, 3] + R - np.sqrt(np.where(inside, R * R - rho2, 0.0)) - Hgel, clip)
+        ref = np.clip(ref, -clip, clip)
+        away = np.abs(np.sqrt(rho2) - R) > 1e-5                  # the scan step can miss a sliver at the rim
+        assert inside.sum() > 40 and (~inside).sum() > 40
+        assert np.abs(h - ref)[away].max() < 1e-12
+        assert h.min() < 0.0                                     # the pressed centre is below the gel top
