@@ -1,0 +1,74 @@
+"""Host logic of the surrogate pipeline (paper_2405_02914_gb300/surrogate.py)
+on the CPU: the keyframe trajectory it reads poses from, the per-frame
+loading scalars fed to the network, and the fallback rule whose served-rate
+summary the benchmark reports.  Expected values are worked by hand from the
+definitions in the docstrings."""
+import numpy as np
+import pytest
+
+from paper_2405_02914_gb300 import inputs as I
+from paper_2405_02914_gb300 import surrogate as G
+
+
+def _kf():
+    # press 0.4 mm in 100 substeps, slip 0.5 mm along +x in 200, turn 0.3 rad in 100
+    return I.press_slip_rotate((1e-3, 2e-3, 5e-3), 0.4e-3, 0.5e-3, 0.3, 100, 200, 100)
+
+
+@pytest.mark.parametrize("k,tip,yaw", [
+    (-5, (1e-3, 2e-3, 5e-3), 0.0),              # before the first keyframe: the first pose
+    (0, (1e-3, 2e-3, 5e-3), 0.0),
+    (50, (1e-3, 2e-3, 4.8e-3), 0.0),            # half way down
+    (100, (1e-3, 2e-3, 4.6e-3), 0.0),
+    (200, (1.25e-3, 2e-3, 4.6e-3), 0.0),        # half way along the slip
+    (300, (1.5e-3, 2e-3, 4.6e-3), 0.0),
+    (350, (1.5e-3, 2e-3, 4.6e-3), 0.15),        # half way through the turn
+    (400, (1.5e-3, 2e-3, 4.6e-3), 0.3),
+    (10**6, (1.5e-3, 2e-3, 4.6e-3), 0.3),       # after the last keyframe: the last pose
+])
+def test_trajectory_state_is_piecewise_linear(k, tip, yaw):
+    t, y = G.trajectory_state(_kf(), k)
+    # keyframes are stored as float32 values (the kernels read float32 poses)
+    np.testing.assert_allclose(t, tip, rtol=0, atol=1e-9)
+    assert y == pytest.approx(yaw, abs=1e-7)
+
+
+def test_frame_scalars_by_phase():
+    sc = I.scene_small(cx=16, cy=16, cz=4, press=0.3e-3, slip=0.4e-3, rotate=0.2, n_press=100, n_slip=200,
+                       n_rot=100, mu=1.0, E=2.4e5, nu=0.46)
+    H, dx = sc.gel.height, sc.gel.dx
+    descent = 0.3e-3 + 0.37 * dx                # the tip starts 0.37 cells above the gel
+    mm_per_ks = 1e-3 * 1e-3                      # rates are in mm per 1000 substeps
+    # mid-press: depth below the gel top, descent rate, no tangential motion
+    s = G.frame_scalars(sc, 60)
+    tip_z = H + 0.37 * dx - 0.6 * descent
+    assert s[0] == pytest.approx(max(0.0, H - tip_z) / 1e-3, rel=1e-5)
+    assert s[7] == pytest.approx(descent / 100 / mm_per_ks, rel=1e-5)
+    assert s[1] == 0 and s[2] == 0 and s[3] == 0 and s[8] == 0
+    # material constants centred on their ranges
+    assert s[4] == pytest.approx((2.4e5 - 1.9e5) / 1e5, rel=1e-6)
+    assert s[5] == pytest.approx((0.46 - 0.44) / 0.04, rel=1e-5)
+    assert s[6] == pytest.approx((1.0 - 0.6) / 0.4, rel=1e-6)
+    # mid-slip: full press depth, slip so far along +x, slip speed as the tangential rate
+    s = G.frame_scalars(sc, 200)
+    assert s[0] == pytest.approx(0.3, rel=1e-4)
+    assert s[1] == pytest.approx(0.2, rel=1e-4) and abs(s[2]) < 1e-6 and s[3] == 0
+    assert s[7] == pytest.approx(0.0, abs=1e-6)
+    assert s[8] == pytest.approx(0.4e-3 / 200 / mm_per_ks, rel=1e-4)
+    # mid-turn: the rotation so far, and its speed at 3 mm from the axis
+    s = G.frame_scalars(sc, 350)
+    assert s[1] == pytest.approx(0.4, rel=1e-4) and s[3] == pytest.approx(0.1, rel=1e-5)
+    assert s[8] == pytest.approx(0.2 / 100 * 3e-3 / mm_per_ks, rel=1e-4)
+
+
+def test_serve_summary_hand_worked():
+    err = np.array([0.01, 0.03, 0.05, 0.015])
+    ind = np.array([0.01, 0.05, 0.01, 0.03])
+    s = G.serve_summary(err, ind, threshold=0.02)
+    # frames 1 and 3 exceed the indicator threshold and go to the simulator
+    assert s["n"] == 4 and s["fallback_frac"] == 0.5
+    # served errors [0.01, 0, 0.05, 0]: three of four within 2 %
+    assert s["served_within"] == 0.75 and s["max_served_err"] == 0.05
+    # the network alone: 0.01 and 0.015 within 2 %
+    assert s["surrogate_within"] == 0.5
+    assert s["median_err"] == pytest.approx(0.0225) and s["p90_err"] == pytest.approx(0.044)
