@@ -233,6 +233,42 @@ def test_energy_balance_free_oscillation():
     assert peak_pe > 0.7
 
 
+@pytest.mark.parametrize("base", [I.BASE_FIXED, I.BASE_SLIP, I.BASE_FREE])
+def test_grid_update_boundary_rules(base):
+    """Eq. 5 and the boundary rules on a grid with known momenta: a node with
+    mass gets V = MG / M + dt g; a massless node stays at rest; the two-node
+    padding ring at -x, +x, -y, +y and +z is held at rest; nodes at or below
+    the gel base (physical z index <= 0) are held at rest (fixed base), lose
+    only their normal component (slip base) or keep their velocity (free).
+    A ring one node too wide or narrow, a base plane one node off or a
+    swapped axis fails this."""
+    sc = _scene(cx=8, cy=12, cz=4, g=(0.0, 0.0, -9.81), base=base)
+    s = O.make_scene(sc)
+    nx, ny, nz = sc.gel.nodes
+    assert nx != ny                                   # so that swapped axes show
+    ox, oy, oz = sc.gel.origin
+    nn = nx * ny * nz
+    rng = np.random.default_rng(9)
+    M = rng.uniform(0.5, 2.0, nn)
+    M[rng.random(nn) < 0.1] = 0.0                      # some empty nodes
+    u = rng.standard_normal((nn, 3))
+    V, cnt = O.grid_update(s, O.make_indenter(I.no_indenter()), O.pose(sc.keyframes, 0, s.dt, 0.0),
+                           M, M[:, None] * u)
+    assert cnt == 0
+    az, ay, ax = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    az, ay, ax = az.ravel(), ay.ravel(), ax.ravel()
+    ref = np.where(M[:, None] > 0, u + s.dt * np.array([0.0, 0.0, -9.81]), 0.0)
+    ring = (ax < 2) | (ay < 2) | (ax >= nx - 2) | (ay >= ny - 2) | (az >= nz - 2)
+    ref[ring] = 0.0
+    low = (az - oz <= 0) & ~ring
+    if base == I.BASE_FIXED:
+        ref[low] = 0.0
+    elif base == I.BASE_SLIP:
+        ref[low, 2] = 0.0
+    assert low.sum() > 0 and ring.sum() > 0 and (~ring & ~low & (M > 0)).sum() > 0
+    assert np.abs(V - ref).max() <= 1e-15 * np.abs(ref).max() + 1e-300
+
+
 def test_uniaxial_compression_linear_elasticity():
     """Block on a frictionless base pressed slowly by a frictionless plate to
     strain 1e-3: interior stress is uniaxial, sigma_zz = E eps_zz (2%) and the
