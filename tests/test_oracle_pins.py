@@ -175,6 +175,28 @@ def test_affine_field_transfers_exactly():
     assert np.abs(Cm - A.reshape(9)).max() < 1e-9 * np.abs(A).max()
 
 
+@pytest.mark.parametrize("base", [I.BASE_FIXED, I.BASE_SLIP, I.BASE_FREE])
+def test_g2p_uniform_field_and_bottom_rule(base):
+    """A uniform grid velocity u comes back as v = u with C = 0 at every
+    particle (the weights sum to one and their first moment vanishes),
+    except that Algorithm 1 zeroes v_z of the bottom-layer particles when the
+    base is not free."""
+    sc = _scene(g=(0.0, 0.0, 0.0), base=base)
+    s = O.make_scene(sc)
+    st = _state(sc)
+    u = np.array([0.3, -0.2, 0.5])
+    nx, ny, nz = sc.gel.nodes
+    V = np.tile(u, (nx * ny * nz, 1))
+    v, Cm = O.g2p(s, st, V)
+    bottom = (st.tag & I.TAG_BOTTOM) != 0
+    assert 0 < bottom.sum() < st.n
+    ref = np.tile(u, (st.n, 1))
+    if base != I.BASE_FREE:
+        ref[bottom, 2] = 0.0
+    assert np.abs(v - ref).max() < 1e-14
+    assert np.abs(Cm).max() < 1e-9 * np.abs(u).max() * 4.0 / sc.gel.dx
+
+
 # ------------------------------------------------------------------ full steps (Algorithm 1)
 
 def test_free_fall_closed_form():
