@@ -32,7 +32,8 @@
  * against finite differences of its energy, rotation covariance and Hooke's
  * law; P2G mass, momentum and APIC angular momentum; exact transfer of
  * affine velocity fields; Eq. 5 with gravity and the wall-ring and base
- * rules on a grid of known momenta; free fall in closed form; energy balance of a free
+ * rules on a grid of known momenta; G2P of a uniform field with the
+ * bottom-layer rule; free fall in closed form; energy balance of a free
  * elastic oscillation; uniaxial compression against linear elasticity; SDF
  * surface points, eikonal property and gradients; contact projection
  * invariants; surface readout closed forms; the displacement splat (rigid
