@@ -694,19 +694,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // G[k][c][b][r][xo] = src[b][r][xs(xo, k)][c] (zero where xs leaves the
 // image), k < nk; mode 0: xs = xo + k - off, mode 1: xs = 2 xo + k - off,
 // mode 2: u = xo + k - off inside [0, wout), xs = u >> 1.  A thread takes
-// four channels (8-byte loads) of eight consecutive xo and writes four
+// eight channels (16-byte loads) of eight consecutive xo and writes eight
 // 16-byte runs, one per channel; the channel groups run fastest across
 // threads so that the loads of a warp are contiguous.  b runs over the
 // batch B, the layout keeps maxB images; ch is a multiple of 8.
 __global__ void k_wg_gather(const bf16 *__restrict__ src, bf16 *__restrict__ dst, int B, int maxB, int rows,
                             int win, int wout, int ch, int nk, int off, int mode)
 {
-    const int ng = wout / 8, cq = ch / 4;
+    const int ng = wout / 8, cq = ch / 8;
     const long long total = (long long)nk * B * rows * ng * cq;
     const long long cstride = (long long)maxB * rows * wout;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const int c = 4 * (int)(i % cq);
+        const int c = 8 * (int)(i % cq);
         long long rest = i / cq;
         const int xg = (int)(rest % ng);
         rest /= ng;
@@ -714,7 +714,7 @@ __global__ void k_wg_gather(const bf16 *__restrict__ src, bf16 *__restrict__ dst
         rest /= rows;
         const int b = (int)(rest % B);
         const int k = (int)(rest / B);
-        uint4 ov[4];
+        uint4 ov[8];
         bf16 *oe = reinterpret_cast<bf16 *>(ov);      // oe[q * 8 + j]: channel c + q, pixel j
         const bf16 *srow = src + ((long long)b * rows + r) * win * ch + c;
 #pragma unroll
@@ -730,15 +730,15 @@ __global__ void k_wg_gather(const bf16 *__restrict__ src, bf16 *__restrict__ dst
                 xs = (mode == 1 ? 2 * xo : xo) + k - off;
                 in = xs >= 0 && xs < win;
             }
-            uint2 v = make_uint2(0u, 0u);
-            if (in) v = *reinterpret_cast<const uint2 *>(srow + (long long)xs * ch);
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (in) v = *reinterpret_cast<const uint4 *>(srow + (long long)xs * ch);
             const bf16 *ve = reinterpret_cast<const bf16 *>(&v);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) oe[q * 8 + j] = ve[q];
+            for (int q = 0; q < 8; ++q) oe[q * 8 + j] = ve[q];
         }
         bf16 *d0 = dst + ((((long long)k * ch + c) * maxB + b) * rows + r) * wout + xg * 8;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4 *>(d0 + q * cstride) = ov[q];
+        for (int q = 0; q < 8; ++q) *reinterpret_cast<uint4 *>(d0 + q * cstride) = ov[q];
     }
 }
 
@@ -1425,10 +1425,10 @@ static void launch_wgrad_tc(tsurr_net *n, int L, int B)
     const int up = n->up[L], st = n->stride[L], ci = n->cin[L], co = n->cout[L];
     const int wout = w.nseg * w.kw, rows = n->hin[L];
     const unsigned gmax = (unsigned)(8 * n->num_sms);
-    const long long ty = (long long)B * w.hout * (wout / 8) * (co / 4);
+    const long long ty = (long long)B * w.hout * (wout / 8) * (co / 8);
     k_wg_gather<<<std::min(cdiv(ty, 256), gmax), 256, 0, n->s>>>(n->dpre, n->dyt, B, n->maxB, w.hout, wout, wout, co,
                                                                   1, 0, 0);
-    const long long tg = 3LL * B * rows * (wout / 8) * (ci / 4);
+    const long long tg = 3LL * B * rows * (wout / 8) * (ci / 8);
     k_wg_gather<<<std::min(cdiv(tg, 256), gmax), 256, 0, n->s>>>(n->act[n->src[L]], n->gx, B, n->maxB, rows,
                                                                   n->win[L], wout, ci, 3, 1, up ? 2 : (st == 2 ? 1 : 0));
     const int cps = 64 / w.kw;
