@@ -65,3 +65,28 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     assert b.run_reference(None, None) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_carries_the_contract_keys(monkeypatch, capsys):
+    """The reference arm (the FP64 oracle on the host cores) prints one JSON
+    line with the same metric and unit as the GPU arm, its own cpu_baseline
+    and an e2e object without host-device traffic."""
+    import json
+    import types
+    from paper_2405_02914_gb300 import inputs as I
+    b = _bench()
+    monkeypatch.setenv("RANK", "0")
+    args = types.SimpleNamespace(gpus=1, steps=2, warmup=3)
+    b.run_reference(args, I.scene_small(cx=8, cy=8, cz=4, n_press=10))
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == b.METRIC and d["unit"] == b.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "workload" in d["config"]
