@@ -53,7 +53,11 @@ typedef struct tsurr_net tsurr_net;
 
 /* Network for batches of up to max_batch images of height x width pixels
  * (multiples of 8, at most 512); allocates parameters, gradients, Adam
- * state and activations. */
+ * state, activations and their FP32 gradients, and the channel-major copies
+ * of the weight-gradient operands (the output gradient, and three
+ * column-shifted copies of the largest layer input), all sized for
+ * max_batch: about 1.3 KB of device memory per pixel of max_batch x height
+ * x width (5.2 GB at 256 x 128 x 128).  TSIM_ERR_OOM if that does not fit. */
 int tsurr_create(int max_batch, int height, int width, void *stream, tsurr_net **out);
 
 /* Number of FP32 parameters (layout above). */
