@@ -40,7 +40,10 @@
  * translation, linear fields, untagged and unreached pixels); the sphere's
  * underside height map; keyframe interpolation; the
  * relative-rest loop (a pure press accepts every first pass; a sticking
- * slip needs repeated passes); a sticking slip or turn drags the contact
+ * slip needs repeated passes); the relative-rest check itself on
+ * hand-worked slip and turn states (threshold x the object's tangential
+ * speed, xy components only, the out-of-contact and no-tangential-motion
+ * accepts); a sticking slip or turn drags the contact
  * patch the indenter's way by less than the indenter moved, and without
  * friction it stays in place.
  * Partly unpinned: the exact lag of the gel behind a sticking indenter over

@@ -239,6 +239,14 @@ def nearest(x, xo) -> int:
     return lib().orc_nearest(x.shape[0], x, np.ascontiguousarray(xo, dtype=np.float64))
 
 
+def relrest_accept(s: Scene, ind: Indenter, ps: Pose, xe, ve) -> bool:
+    """Algorithm 1's relative-rest check at the calibration particle x_e with
+    velocity v_e (True: accept the pass)."""
+    return bool(lib().orc_relrest_accept(C.byref(s), C.byref(ind), C.byref(ps),
+                                         np.ascontiguousarray(xe, dtype=np.float64),
+                                         np.ascontiguousarray(ve, dtype=np.float64)))
+
+
 def substep(s: Scene, ind: Indenter, kf, k: int, st: State):
     """One IMPM time step in place; returns (passes, x_e index, contact nodes)."""
     nn = n_nodes(s)

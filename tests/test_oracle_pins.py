@@ -518,6 +518,93 @@ def test_sticky_slip_needs_extra_passes():
     assert pl[20:].max() > 1
 
 
+def _check_pose(c, vlin=(0.0, 0.0, 0.0), omega=0.0):
+    """A pose at yaw 0 whose SDF centre is c (the sphere's tip below it)."""
+    ps = O.Pose()
+    for a in range(3):
+        ps.c[a] = c[a]
+        ps.tip[a] = c[a]
+        ps.vlin[a] = vlin[a]
+    ps.yaw, ps.cs, ps.sn, ps.omega = 0.0, 1.0, 0.0, omega
+    return ps
+
+
+def _check_setup(threshold=0.5):
+    dx, R = 0.5e-3, 2e-3
+    sc = _scene(dx=dx)
+    s = O.make_scene(sc)
+    s.threshold = threshold
+    ind = O.make_indenter(I.sphere(R, 0.5))
+    c = np.array([10e-3, 10e-3, 7e-3])
+    return s, ind, c, dx, R
+
+
+def test_relrest_check_hand_worked_slip():
+    """Algorithm 1's check at x_e during a slip (v_o = v_lin = 0.1 m/s along
+    x, x_e inside the sphere): the tangential mismatch |v_e,t - v_o,t| is
+    compared with threshold (0.5) x |v_o,t| -- the object's tangential speed,
+    not the particle's -- and the vertical components play no part.  Worked
+    by hand: a mismatch of 0.45 |v_o,t| accepts and 0.55 rejects, whichever
+    direction it points; v_e,t = 0.6 v_o,t (mismatch 0.4) accepts although
+    0.4 > 0.5 x |v_e,t|, and v_e,t = 1.6 v_o,t (mismatch 0.6) rejects
+    although 0.6 <= 0.5 x |v_e,t|."""
+    s, ind, c, dx, R = _check_setup()
+    vo = np.array([0.1, 0.0, 0.0])
+    ps = _check_pose(c, vlin=vo)
+    xe = c + np.array([0.0, 0.0, -(R - 0.1 * dx)])          # phi = -0.1 dx: in contact
+    assert O.sdf(ind, ps, xe)[0] == pytest.approx(-0.1 * dx, abs=1e-12)
+    for u in ([1.0, 0.0], [0.0, 1.0], [-0.6, 0.8]):
+        u = np.array(u + [0.0])
+        assert O.relrest_accept(s, ind, ps, xe, vo + 0.045 * u)
+        assert not O.relrest_accept(s, ind, ps, xe, vo + 0.055 * u)
+    assert O.relrest_accept(s, ind, ps, xe, [0.06, 0.0, 0.0])
+    assert not O.relrest_accept(s, ind, ps, xe, [0.16, 0.0, 0.0])
+    assert O.relrest_accept(s, ind, ps, xe, [0.11, 0.0, 5.0])      # v_z is not compared
+    assert O.relrest_accept(s, ind, ps, xe, [0.1, 0.0, -5.0])
+    # the threshold scales the bound: at 0.4 the 0.45 mismatch rejects
+    s4, _, _, _, _ = _check_setup(threshold=0.4)
+    assert not O.relrest_accept(s4, ind, ps, xe, vo + [0.045, 0.0, 0.0])
+    assert O.relrest_accept(s4, ind, ps, xe, vo + [0.035, 0.0, 0.0])
+
+
+def test_relrest_check_hand_worked_rotation():
+    """During a turn (v_lin = 0, omega = 2 rad/s about the vertical axis
+    through the centre) the object velocity at x_e = c + (r, 0, .) is
+    omega z x (x_e - c) = (0, omega r, 0): a particle moving with it accepts,
+    one moving the opposite way (mismatch 2 omega r) or not at all (mismatch
+    omega r > 0.5 omega r) rejects."""
+    s, ind, c, dx, R = _check_setup()
+    om, r = 2.0, 1.5e-3
+    ps = _check_pose(c, omega=om)
+    xe = c + np.array([r, 0.0, -np.sqrt(R ** 2 - r ** 2) + 0.2 * dx])
+    assert O.sdf(ind, ps, xe)[0] < 0.0
+    assert O.relrest_accept(s, ind, ps, xe, [0.0, om * r, 0.0])
+    assert O.relrest_accept(s, ind, ps, xe, [0.3 * om * r, 0.8 * om * r, 0.0])   # mismatch 0.36 omega r
+    assert not O.relrest_accept(s, ind, ps, xe, [0.0, -om * r, 0.0])
+    assert not O.relrest_accept(s, ind, ps, xe, [0.0, 0.0, 0.0])
+    assert not O.relrest_accept(s, ind, ps, xe, [om * r, 0.0, 0.0])          # right speed, wrong direction
+
+
+def test_relrest_check_accepts_out_of_contact_and_without_tangential_motion():
+    """The two early accepts of the reading of Algorithm 1: x_e more than one
+    cell away from the object (phi(x_e) > dx), and an object with no
+    tangential velocity at x_e (|v_o,t| < 1e-6 m/s, a pure press); just
+    inside those bounds the same mismatched particle rejects."""
+    s, ind, c, dx, R = _check_setup()
+    ps = _check_pose(c, vlin=(0.1, 0.0, 0.0))
+    for gap, ok in ((1.5, True), (1.05, True), (0.9, False), (0.0, False)):
+        xe = c + np.array([0.0, 0.0, -(R + gap * dx)])
+        assert O.sdf(ind, ps, xe)[0] == pytest.approx(gap * dx, abs=1e-12)
+        assert O.relrest_accept(s, ind, ps, xe, [0.0, 0.0, 0.0]) is ok, gap
+    xe = c + np.array([0.0, 0.0, -(R - 0.1 * dx)])
+    press = _check_pose(c, vlin=(0.0, 0.0, -0.05))
+    assert O.relrest_accept(s, ind, press, xe, [0.3, 0.2, 0.0])
+    assert O.relrest_accept(s, ind, _check_pose(c, vlin=(5e-7, 0.0, -0.05)), xe, [0.3, 0.2, 0.0])
+    assert not O.relrest_accept(s, ind, _check_pose(c, vlin=(2e-6, 0.0, -0.05)), xe, [0.3, 0.2, 0.0])
+    none = O.make_indenter(I.no_indenter())
+    assert O.relrest_accept(s, none, ps, xe, [0.3, 0.2, 0.0])
+
+
 def test_frictionless_sphere_rotation_invariance():
     """A frictionless sphere spinning about its vertical axis exerts no
     tangential force (plain MPM): the surface field is unchanged."""
