@@ -287,16 +287,21 @@ int tsim_kernel_time(tsim_ctx *ctx, int64_t *launches, double *total_ms);
  * gel, mat: host descriptors (node box a multiple of 4 in every direction,
  * at most TSIM_NOALLOC_MAX_BLOCKS 4x4x4 cell blocks); dt: substep of the
  * stress impulse of Eq. 4; x[n*3], v[n*3], C[n*9], F[n*9]: device arrays in
- * the layout of tsim_write_particles, 1 <= n <= TSIM_NOALLOC_MAX_PARTICLES;
- * grid[nx*ny*nz*4]: device output, 16-byte aligned, (M, MG) per node, x
- * fastest (overwritten); stream: cudaStream_t or NULL.
- * Sizes beyond the maxima return TSIM_ERR_INVALID_ARG before any GPU work.
+ * the layout of tsim_write_particles, 1 <= n <= TSIM_NOALLOC_MAX_PARTICLES,
+ * each 4-byte aligned; grid[nx*ny*nz*4]: device output, 16-byte aligned,
+ * (M, MG) per node, x fastest (overwritten); stream: cudaStream_t or NULL.
+ * All five arrays must be device memory of the current device or managed
+ * memory.  Sizes beyond the maxima, misaligned arrays and host pointers
+ * return TSIM_ERR_INVALID_ARG before any GPU work.
  * Particles outside the node box give TSIM_ERR_DOMAIN, J <= 0 gives
  * TSIM_ERR_NUMERIC.  The call waits for its work on the stream before it
- * returns.  It never allocates: the first call on a device looks up the
- * scratch address for that device (make that first call before any stream
- * capture); every call shares the scratch and clears what must start at
- * zero, so calls that overlap on the GPU race and must be serialised. */
+ * returns.  It never allocates through the caller's allocator: the first
+ * call on a device loads the library's device module there (CUDA loads
+ * modules lazily by default), which reserves the scratch on that device, and
+ * looks up its address -- so that first call may synchronise the device;
+ * make it before any stream capture.  Every call shares the scratch and
+ * clears what must start at zero, so calls that overlap on the GPU race and
+ * must be serialised. */
 #define TSIM_NOALLOC_MAX_PARTICLES (1 << 20)
 #define TSIM_NOALLOC_MAX_BLOCKS (1 << 15)
 #define TSIM_NOALLOC_SCRATCH_BYTES (3 * 4 * TSIM_NOALLOC_MAX_BLOCKS + 4 * TSIM_NOALLOC_MAX_PARTICLES + 256)

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -41,10 +42,13 @@ static_assert(NA_BYTES == TSIM_NOALLOC_SCRATCH_BYTES, "scratch size must match t
 
 }  // namespace
 
-// The scratch: one copy per device, reserved when the library's module loads.
-// In host code this name is only a stand-in, never a device address; host
-// code uses the address that cudaGetSymbolAddress returns for the current
-// device.
+// The scratch: one copy per device.  With CUDA's lazy module loading (the
+// default) the module that holds it is loaded on a device, and the array
+// reserved there, at the first call on that device (its
+// cudaGetSymbolAddress); that first call may therefore synchronise the
+// device and take the array's memory.  In host code this name is only a
+// stand-in, never a device address; host code uses the address that
+// cudaGetSymbolAddress returns for the current device.
 static __device__ __align__(256) unsigned char g_tsim_noalloc_scratch[NA_BYTES];
 
 namespace {
@@ -254,6 +258,28 @@ extern "C" int tsim_p2g_noalloc(const tsim_gel_desc *gel, const tsim_material *m
     if (!(mat->E > 0.f) || !(mat->nu >= 0.f && mat->nu < 0.5f) || !(mat->rho > 0.f) || !(dt > 0.f))
         return na_fail(TSIM_ERR_INVALID_ARG, "tsim_p2g_noalloc: need E > 0, 0 <= nu < 0.5, rho > 0, dt > 0");
     if (!x || !v || !C || !F || !grid) return na_fail(TSIM_ERR_INVALID_ARG, "tsim_p2g_noalloc: null array");
+    // the kernels read x, v, C, F as floats and add to grid with 16-byte vector atomics
+    if ((uintptr_t)grid % 16 != 0)
+        return na_fail(TSIM_ERR_INVALID_ARG, "tsim_p2g_noalloc: grid must be 16-byte aligned");
+    const void *arrays[5] = {x, v, C, F, grid};
+    const char *names[5] = {"x", "v", "C", "F", "grid"};
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return na_fail(TSIM_ERR_CUDA, "tsim_p2g_noalloc: no current device");
+    for (int a = 0; a < 5; ++a) {
+        if ((uintptr_t)arrays[a] % 4 != 0)
+            return na_fail(TSIM_ERR_INVALID_ARG, std::string("tsim_p2g_noalloc: ") + names[a] +
+                                                     " must be 4-byte aligned");
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, arrays[a]) != cudaSuccess) {
+            cudaGetLastError();
+            return na_fail(TSIM_ERR_INVALID_ARG, std::string("tsim_p2g_noalloc: ") + names[a] +
+                                                     " is not a pointer the CUDA runtime knows");
+        }
+        const bool ok = at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == cur);
+        if (!ok)
+            return na_fail(TSIM_ERR_INVALID_ARG, std::string("tsim_p2g_noalloc: ") + names[a] +
+                                                     " must be device memory of the current device (or managed)");
+    }
 
     unsigned char *scr = nullptr;
     cudaError_t e = scratch_address(&scr);

@@ -72,3 +72,36 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     big = T.gel_desc(I.Gel(256, 256, 64, 1e-3))                # more cell blocks than the scratch holds
     rc = L.tsim_p2g_noalloc(C.byref(big), C.byref(mat), C.c_float(1e-5), p, p, p, p, 8, p, None)
     assert rc == 1 and b"cell blocks" in L.tsim_last_error()
+
+
+def test_noalloc_rejects_misaligned_and_host_arrays():
+    """Arrays the kernels cannot use are refused before any GPU work: a grid
+    that is not 16-byte aligned (its float4 atomics would fault), a particle
+    array off a 4-byte boundary, and host memory in place of device memory."""
+    torch = pytest.importorskip("torch")
+    L = T.load()
+    sc = I.scene_small(cx=4, cy=4, cz=2)
+    gel, mat = T.gel_desc(sc.gel), T.material_desc(sc.mat)
+    n = sc.gel.n_particles
+    nn = int(np.prod(sc.gel.nodes))
+    # every buffer is large enough for the call, so nothing reads out of bounds
+    parts = torch.zeros(n * 9 + 16, device="cuda")
+    grid = torch.zeros(nn * 4 + 16, device="cuda")
+    p = C.c_void_p(parts.data_ptr())
+    dt = C.c_float(1e-5)
+
+    def call(x, g):
+        return L.tsim_p2g_noalloc(C.byref(gel), C.byref(mat), dt, x, p, p, p, n, g, None)
+
+    rc = call(p, C.c_void_p(grid.data_ptr() + 4))
+    assert rc == 1 and b"16-byte" in L.tsim_last_error()
+    rc = call(C.c_void_p(parts.data_ptr() + 2), C.c_void_p(grid.data_ptr()))
+    assert rc == 1 and b"4-byte" in L.tsim_last_error()
+    host = np.zeros(nn * 4 + 16, dtype=np.float32)
+    rc = call(p, C.c_void_p(host.ctypes.data))
+    assert rc == 1 and b"device memory" in L.tsim_last_error()
+    hx = np.zeros(n * 9 + 16, dtype=np.float32)
+    rc = call(C.c_void_p(hx.ctypes.data), C.c_void_p(grid.data_ptr()))
+    assert rc == 1 and b"device memory" in L.tsim_last_error()
+    # the same aligned device buffers pass the checks (F = 0 then gives J = 0)
+    assert call(p, C.c_void_p(grid.data_ptr())) == 4, L.tsim_last_error()
