@@ -54,6 +54,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_TAG_BOTTOM 0x80000000u
 #define ORC_TAG_TOP 0x40000000u
@@ -346,17 +349,17 @@ static long node_index(const orc_scene *s, int ax, int ay, int az)
     return ((long)az * s->ny + ay) * s->nx + ax;
 }
 
-/* Particle-to-grid: Eq. 1 (mass) and Eqs. 2-4 (momentum MG = MM + ME). */
-int orc_p2g(const orc_scene *s, int n, const double *x, const double *v,
-            const double *C, const double *F, double *M, double *MG)
+/* Particle-to-grid, Eq. 1 (mass) and Eqs. 2-4 (momentum MG = MM + ME), of
+ * particles p0..p1-1 added to M and MG laid out over the node sub-box whose
+ * first node is lo[3] (box indices) and whose extent is dim[3]. */
+static int p2g_range(const orc_scene *s, int p0, int p1, const double *x, const double *v,
+                     const double *C, const double *F, const int lo[3], const int dim[3],
+                     double *M, double *MG)
 {
-    long nn = (long)s->nx * s->ny * s->nz;
-    memset(M, 0, sizeof(double) * nn);
-    memset(MG, 0, sizeof(double) * 3 * nn);
     double dx = s->dx, V0 = dx * dx * dx / s->ppc, mp = s->rho * V0, mu, lam;
     orc_lame(s->E, s->nu, &mu, &lam);
     double kME = -4.0 * s->dt / (dx * dx);
-    for (int p = 0; p < n; ++p) {
+    for (int p = p0; p < p1; ++p) {
         int base[3];
         double w[3][3], tau[9];
         for (int a = 0; a < 3; ++a) orc_weights(x[p * 3 + a], dx, &base[a], w[a]);
@@ -368,7 +371,10 @@ int orc_p2g(const orc_scene *s, int n, const double *x, const double *v,
                     int ax = base[0] + i + s->ox, ay = base[1] + j + s->oy, az = base[2] + k + s->oz;
                     if (ax < 0 || ay < 0 || az < 0 || ax >= s->nx || ay >= s->ny || az >= s->nz)
                         return ORC_ERR_DOMAIN;
-                    long ni = node_index(s, ax, ay, az);
+                    int lx = ax - lo[0], ly = ay - lo[1], lz = az - lo[2];
+                    if (lx < 0 || ly < 0 || lz < 0 || lx >= dim[0] || ly >= dim[1] || lz >= dim[2])
+                        return ORC_ERR_ARG;
+                    long ni = ((long)lz * dim[1] + ly) * dim[0] + lx;
                     double wip = w[0][i] * w[1][j] * w[2][k];
                     double d[3] = {(base[0] + i) * dx - x[p * 3 + 0],
                                    (base[1] + j) * dx - x[p * 3 + 1],
@@ -386,14 +392,26 @@ int orc_p2g(const orc_scene *s, int n, const double *x, const double *v,
     return ORC_OK;
 }
 
+/* Particle-to-grid of all particles in index order (the grid is cleared first). */
+int orc_p2g(const orc_scene *s, int n, const double *x, const double *v,
+            const double *C, const double *F, double *M, double *MG)
+{
+    long nn = (long)s->nx * s->ny * s->nz;
+    memset(M, 0, sizeof(double) * nn);
+    memset(MG, 0, sizeof(double) * 3 * nn);
+    const int lo[3] = {0, 0, 0}, dim[3] = {s->nx, s->ny, s->nz};
+    return p2g_range(s, 0, n, x, v, C, F, lo, dim, M, MG);
+}
+
 /* ------------------------------------------------------------------ grid */
 
-/* Grid velocity (Eq. 5) + gravity, indenter contact, walls, fixed base. */
-int orc_grid_update(const orc_scene *s, const orc_indenter *ind, const orc_pose *ps,
-                    const double *M, const double *MG, double *V, long *n_contact)
+/* Grid velocity (Eq. 5) + gravity, indenter contact, walls, fixed base, on
+ * the node planes z0 <= az < z1; returns the number of contact nodes. */
+static long grid_update_planes(const orc_scene *s, const orc_indenter *ind, const orc_pose *ps,
+                               const double *M, const double *MG, double *V, int z0, int z1)
 {
     long cnt = 0;
-    for (int az = 0; az < s->nz; ++az)
+    for (int az = z0; az < z1; ++az)
         for (int ay = 0; ay < s->ny; ++ay)
             for (int ax = 0; ax < s->nx; ++ax) {
                 long ni = node_index(s, ax, ay, az);
@@ -432,6 +450,13 @@ int orc_grid_update(const orc_scene *s, const orc_indenter *ind, const orc_pose 
                 }
                 V[ni * 3 + 0] = Vn[0]; V[ni * 3 + 1] = Vn[1]; V[ni * 3 + 2] = Vn[2];
             }
+    return cnt;
+}
+
+int orc_grid_update(const orc_scene *s, const orc_indenter *ind, const orc_pose *ps,
+                    const double *M, const double *MG, double *V, long *n_contact)
+{
+    long cnt = grid_update_planes(s, ind, ps, M, MG, V, 0, s->nz);
     if (n_contact) *n_contact = cnt;
     return ORC_OK;
 }
@@ -569,6 +594,189 @@ int orc_run(const orc_scene *s, const orc_indenter *ind, const double *kf, int n
         if (pass_log) pass_log[t] = ps;
         if (e_log) e_log[t] = e;
     }
+    free(M); free(MG); free(V);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ all-cores variant */
+
+/* Threads that orc_run_par uses by default (1 without OpenMP). */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+typedef struct {
+    int p0, p1;              /* particle chunk */
+    int lo[3], dim[3];       /* node sub-box covered by the chunk's stencils */
+    double *M, *MG;          /* private grid over that box */
+    size_t cap;              /* nodes allocated */
+    int rc;
+} orc_chunk;
+
+/* P2G of one chunk into its private grid: the sub-box is the bounding box of
+ * the chunk's 3x3x3 stencils. */
+static void chunk_p2g(const orc_scene *s, orc_chunk *c, const double *x, const double *v,
+                      const double *C, const double *F)
+{
+    int mn[3] = {s->nx, s->ny, s->nz}, mx[3] = {-1, -1, -1};
+    const int off[3] = {s->ox, s->oy, s->oz};
+    for (int p = c->p0; p < c->p1; ++p)
+        for (int a = 0; a < 3; ++a) {
+            int b;
+            double w[3];
+            orc_weights(x[p * 3 + a], s->dx, &b, w);
+            b += off[a];
+            if (b < mn[a]) mn[a] = b;
+            if (b + 2 > mx[a]) mx[a] = b + 2;
+        }
+    if (c->p1 <= c->p0) { c->rc = ORC_OK; c->dim[0] = c->dim[1] = c->dim[2] = 0; return; }
+    size_t nodes = 1;
+    for (int a = 0; a < 3; ++a) {
+        c->lo[a] = mn[a];
+        c->dim[a] = mx[a] - mn[a] + 1;
+        nodes *= (size_t)c->dim[a];
+    }
+    if (nodes > c->cap) {
+        free(c->M); free(c->MG);
+        c->M = (double *)malloc(sizeof(double) * nodes);
+        c->MG = (double *)malloc(sizeof(double) * 3 * nodes);
+        c->cap = (c->M && c->MG) ? nodes : 0;
+        if (!c->cap) { c->rc = ORC_ERR_ARG; return; }
+    }
+    memset(c->M, 0, sizeof(double) * nodes);
+    memset(c->MG, 0, sizeof(double) * 3 * nodes);
+    c->rc = p2g_range(s, c->p0, c->p1, x, v, C, F, c->lo, c->dim, c->M, c->MG);
+}
+
+/* The grid sums of Eqs. 1-2 from the chunks' private grids, added in chunk
+ * order, on the node planes z0 <= az < z1. */
+static void reduce_planes(const orc_scene *s, const orc_chunk *ch, int T, double *M, double *MG, int z0, int z1)
+{
+    for (int az = z0; az < z1; ++az)
+        for (int ay = 0; ay < s->ny; ++ay)
+            for (int ax = 0; ax < s->nx; ++ax) {
+                double m = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+                for (int t = 0; t < T; ++t) {
+                    const orc_chunk *c = ch + t;
+                    int lx = ax - c->lo[0], ly = ay - c->lo[1], lz = az - c->lo[2];
+                    if (lx < 0 || ly < 0 || lz < 0 || lx >= c->dim[0] || ly >= c->dim[1] || lz >= c->dim[2])
+                        continue;
+                    long li = ((long)lz * c->dim[1] + ly) * c->dim[0] + lx;
+                    m += c->M[li];
+                    g0 += c->MG[li * 3]; g1 += c->MG[li * 3 + 1]; g2 += c->MG[li * 3 + 2];
+                }
+                long ni = node_index(s, ax, ay, az);
+                M[ni] = m;
+                MG[ni * 3] = g0; MG[ni * 3 + 1] = g1; MG[ni * 3 + 2] = g2;
+            }
+}
+
+/* orc_run with its loops shared among nthreads threads (<= 0: orc_threads()):
+ * particles in nthreads contiguous index chunks, each P2G'd into a private
+ * grid that is summed in chunk order; node and particle loops split by range;
+ * the nearest particle is the chunk minima compared in chunk order (ties go
+ * to the lowest index, as in orc_nearest).  Same arithmetic per particle and
+ * node as orc_run; only the order of the grid sums differs, so results agree
+ * with orc_run to rounding.  Used for the all-cores CPU baseline and for
+ * oracle runs too large for one core. */
+int orc_run_par(const orc_scene *s, const orc_indenter *ind, const double *kf, int nkf, int k0, int nsub,
+                int n, double *x, double *v, double *C, double *F, const uint32_t *tag,
+                int *pass_log, int *e_log, int nthreads)
+{
+    int T = nthreads > 0 ? nthreads : orc_threads();
+    if (T > n) T = n > 0 ? n : 1;
+    long nn = (long)s->nx * s->ny * s->nz;
+    double *M = (double *)malloc(sizeof(double) * nn);
+    double *MG = (double *)malloc(sizeof(double) * 3 * nn);
+    double *V = (double *)malloc(sizeof(double) * 3 * nn);
+    orc_chunk *ch = (orc_chunk *)calloc((size_t)T, sizeof(orc_chunk));
+    int *best = (int *)malloc(sizeof(int) * T), *rcs = (int *)malloc(sizeof(int) * T);
+    double *bestd = (double *)malloc(sizeof(double) * T);
+    int rc = ORC_OK;
+    if (!M || !MG || !V || !ch || !best || !rcs || !bestd) rc = ORC_ERR_ARG;
+    for (int t = 0; rc == ORC_OK && t < T; ++t) {
+        ch[t].p0 = (int)((long)n * t / T);
+        ch[t].p1 = (int)((long)n * (t + 1) / T);
+    }
+    for (int st = 0; rc == ORC_OK && st < nsub; ++st) {
+        orc_pose ps;
+        orc_pose_eval(kf, nkf, k0 + st, s->dt, ind->tip_offset, &ps);
+        /* x_e: nearest particle to the tip */
+#pragma omp parallel for schedule(static, 1) num_threads(T)
+        for (int t = 0; t < T; ++t) {
+            int b = ch[t].p0;
+            double bd = 1e300;
+            for (int p = ch[t].p0; p < ch[t].p1; ++p) {
+                double a = x[p * 3] - ps.tip[0], bb = x[p * 3 + 1] - ps.tip[1], c = x[p * 3 + 2] - ps.tip[2];
+                double d = a * a + bb * bb + c * c;
+                if (d < bd) { bd = d; b = p; }
+            }
+            best[t] = b;
+            bestd[t] = bd;
+        }
+        int e = best[0];
+        double ed = bestd[0];
+        for (int t = 1; t < T; ++t)
+            if (bestd[t] < ed) { ed = bestd[t]; e = best[t]; }
+        int j = 0;
+        for (;;) {
+#pragma omp parallel for schedule(static, 1) num_threads(T)
+            for (int t = 0; t < T; ++t) chunk_p2g(s, ch + t, x, v, C, F);
+            for (int t = 0; t < T; ++t)
+                if (ch[t].rc != ORC_OK && rc == ORC_OK) rc = ch[t].rc;
+            if (rc) break;
+#pragma omp parallel for schedule(static, 1) num_threads(T)
+            for (int t = 0; t < T; ++t) {
+                int z0 = (int)((long)s->nz * t / T), z1 = (int)((long)s->nz * (t + 1) / T);
+                reduce_planes(s, ch, T, M, MG, z0, z1);
+                grid_update_planes(s, ind, &ps, M, MG, V, z0, z1);
+            }
+#pragma omp parallel for schedule(static, 1) num_threads(T)
+            for (int t = 0; t < T; ++t)
+                rcs[t] = orc_g2p(s, ch[t].p1 - ch[t].p0, x + (long)ch[t].p0 * 3, tag + ch[t].p0, V,
+                                 v + (long)ch[t].p0 * 3, C + (long)ch[t].p0 * 9);
+            for (int t = 0; t < T; ++t)
+                if (rcs[t] != ORC_OK && rc == ORC_OK) rc = rcs[t];
+            if (rc) break;
+            int ok = orc_relrest_accept(s, ind, &ps, x + e * 3, v + e * 3);
+            ++j;
+            if (ok || j >= s->limit) break;
+        }
+        if (rc) break;
+#pragma omp parallel for schedule(static, 1) num_threads(T)
+        for (int t = 0; t < T; ++t) {
+            rcs[t] = ORC_OK;
+            for (int p = ch[t].p0; p < ch[t].p1; ++p) {
+                double *Fp = F + (long)p * 9, Fn[9];
+                const double *Cp = C + (long)p * 9;
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) {
+                        double a = Fp[r * 3 + c];
+                        for (int q = 0; q < 3; ++q) a += s->dt * Cp[r * 3 + q] * Fp[q * 3 + c];
+                        Fn[r * 3 + c] = a;                               /* Eq. 8 */
+                    }
+                memcpy(Fp, Fn, sizeof Fn);
+                for (int d = 0; d < 3; ++d) x[(long)p * 3 + d] += s->dt * v[(long)p * 3 + d];   /* Eq. 9 */
+                double J = det3(Fp);
+                if (!(J > 0.0) || !isfinite(J) || !isfinite(x[(long)p * 3]) || !isfinite(x[(long)p * 3 + 1]) ||
+                    !isfinite(x[(long)p * 3 + 2]))
+                    rcs[t] = ORC_ERR_NUMERIC;
+            }
+        }
+        for (int t = 0; t < T; ++t)
+            if (rcs[t] != ORC_OK && rc == ORC_OK) rc = rcs[t];
+        if (rc) break;
+        if (pass_log) pass_log[st] = j;
+        if (e_log) e_log[st] = e;
+    }
+    if (ch)
+        for (int t = 0; t < T; ++t) { free(ch[t].M); free(ch[t].MG); }
+    free(ch); free(best); free(bestd); free(rcs);
     free(M); free(MG); free(V);
     return rc;
 }

@@ -26,8 +26,12 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-o", tmp, _SRC, "-lm"]
+        try:    # OpenMP for orc_run_par (all host cores); without it the same code runs on one
+            subprocess.check_call(cmd[:-1] + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(cmd)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -90,6 +94,10 @@ def lib():
             L.orc_run.argtypes = [P(Scene), P(Indenter), _D, C.c_int, C.c_int, C.c_int, C.c_int,
                                   _D, _D, _D, _D, _U, _I, _I]
             L.orc_run.restype = C.c_int
+            L.orc_run_par.argtypes = [P(Scene), P(Indenter), _D, C.c_int, C.c_int, C.c_int, C.c_int,
+                                      _D, _D, _D, _D, _U, _I, _I, C.c_int]
+            L.orc_run_par.restype = C.c_int
+            L.orc_threads.restype = C.c_int
             L.orc_surface.argtypes = [C.c_int, _D, _U, C.c_int, C.c_int, C.c_double, C.c_double,
                                       _D, _D]
             L.orc_surface_disp.argtypes = [C.c_int, _D, _D, _U, C.c_int, C.c_int, C.c_double, _D]
@@ -268,6 +276,23 @@ def run(s: Scene, ind: Indenter, kf, k0: int, nsub: int, st: State):
     el = np.zeros(max(nsub, 1), dtype=np.int32)
     _check(lib().orc_run(C.byref(s), C.byref(ind), kf, kf.shape[0], int(k0), int(nsub), st.n,
                          st.x, st.v, st.C, st.F, st.tag, pl, el))
+    return pl[:nsub], el[:nsub]
+
+
+def threads() -> int:
+    """Threads run_par uses by default (the host's cores with OpenMP, else 1)."""
+    return int(lib().orc_threads())
+
+
+def run_par(s: Scene, ind: Indenter, kf, k0: int, nsub: int, st: State, nthreads: int = 0):
+    """run() with its loops shared among nthreads host threads (0: all);
+    the grid sums are added per thread chunk, so results equal run()'s to
+    rounding.  Returns (passes per substep, x_e per substep)."""
+    kf = np.ascontiguousarray(kf, dtype=np.float64)
+    pl = np.zeros(max(nsub, 1), dtype=np.int32)
+    el = np.zeros(max(nsub, 1), dtype=np.int32)
+    _check(lib().orc_run_par(C.byref(s), C.byref(ind), kf, kf.shape[0], int(k0), int(nsub), st.n,
+                             st.x, st.v, st.C, st.F, st.tag, pl, el, int(nthreads)))
     return pl[:nsub], el[:nsub]
 
 
