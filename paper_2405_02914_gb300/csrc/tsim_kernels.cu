@@ -214,22 +214,33 @@ __global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle
 
 enum { MODE_PROLOGUE = 0, MODE_ITER = 1, MODE_COMMIT = 2 };
 
-// Shared memory of one cell block (dynamic, ~61 KB).
+// Shared memory of one cell block (dynamic, ~53 KB: four CTAs per SM).
 struct TransferSmem {
     // staged x (0..2), F (3..11) and tag bits (12) of the block's particles (TMA);
     // phase 1 overwrites a particle's entries with its P2G coefficients:
-    // Q (0..8), m v (9..11), fractional offset f of the new position (12..14)
+    // Q (0..8), m v (9..11), fractional offset f of the new position (12..14);
+    // after phase 2 has read them the rows hold the per-warp node slabs
     float P[15][CAP];
     float4 V[GV * GV * GV];        // grid velocities of the G2P window
-    float A[4][GAN];               // P2G window accumulator (M, MG)
     unsigned short idx[CAP];       // particle order sorted by cell
-    unsigned char cell[CAP];       // cell of each particle (255: handled by atomics / invalid)
+    unsigned char cell[CAP];       // cell of each particle (255: handled by global atomics / invalid)
     int ccount[NCELL], coff[NCELL], ccur[NCELL];
     unsigned long long bar;        // mbarrier of the bulk copies
     unsigned long long key[NT / 32];
     float tip[3];
     Inst inst;                     // the instance constants, copied once per CTA
 };
+
+// Per-warp node slab of the P2G combine: warp w holds the 4x4 cells of z layer
+// w, whose 3x3x3 stencils cover 6 x 6 x 3 nodes; rows padded to 8 nodes and a
+// channel stride of 146 floats (= 2 mod 16) put the two channels that the two
+// threads of a cell write in one instruction on disjoint banks.
+constexpr int SLX = 8, SLY = 6, SLZ = 3;
+constexpr int SLCH = 146;
+constexpr int SLAB = 4 * SLCH;
+static_assert(SLCH >= SLX * SLY * SLZ, "slab channel holds 6 x 6 x 3 nodes");
+static_assert((NT / 32) * SLAB <= 15 * CAP, "the slabs fit in the staging rows");
+static_assert(NT == 2 * NCELL && NCELL / (NT / 32) == 16, "two threads per cell, one z layer of cells per warp");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -333,9 +344,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint3
     return false;
 }
 
-// P2G of one particle into the block window with shared atomics (Eqs. 1-4);
-// used for particles whose stencil moved away from their cell.
-__device__ __noinline__ void p2g_atomic(float (*A)[GAN], int wx, int wy, int wz, const float w[3][3],
+// P2G of one particle straight into the grid with global vector atomics
+// (Eqs. 1-4); used for the few particles whose stencil left their cell.
+__device__ __noinline__ void p2g_global(float4 *acc, const Inst &I, int bx, int by, int bz, const float w[3][3],
                                         const float f[3], const float Q[9], const float mv[3], float mp)
 {
     for (int i = 0; i < 3; ++i)
@@ -343,11 +354,10 @@ __device__ __noinline__ void p2g_atomic(float (*A)[GAN], int wx, int wy, int wz,
             for (int k = 0; k < 3; ++k) {
                 const float wt = w[0][i] * w[1][j] * w[2][k];
                 const float d0 = (float)i - f[0], d1 = (float)j - f[1], d2 = (float)k - f[2];
-                const int n = (wz + k) * GAZ + (wy + j) * GA + (wx + i);
-                atomicAdd(&A[0][n], wt * mp);
-                atomicAdd(&A[1][n], wt * (mv[0] + Q[0] * d0 + Q[1] * d1 + Q[2] * d2));
-                atomicAdd(&A[2][n], wt * (mv[1] + Q[3] * d0 + Q[4] * d1 + Q[5] * d2));
-                atomicAdd(&A[3][n], wt * (mv[2] + Q[6] * d0 + Q[7] * d1 + Q[8] * d2));
+                atomicAdd(&acc[node_of(I, bx + i, by + j, bz + k)],
+                          make_float4(wt * mp, wt * (mv[0] + Q[0] * d0 + Q[1] * d1 + Q[2] * d2),
+                                      wt * (mv[1] + Q[3] * d0 + Q[4] * d1 + Q[5] * d2),
+                                      wt * (mv[2] + Q[6] * d0 + Q[7] * d1 + Q[8] * d2)));
             }
 }
 
@@ -358,12 +368,15 @@ __device__ __noinline__ void p2g_atomic(float (*A)[GAN], int wx, int wy, int wz,
 //      re-binning and the write of the moved state; the particle's P2G
 //      coefficients replace its staged data, and a counting sort groups the
 //      particles by cell (the particles of a cell share one 27-node stencil);
-//   2. cell-parallel: two threads per cell accumulate the cell's 27-node
-//      stencil x 4 channels (Eqs. 1-4) in registers over its particles, then
-//      add it to the block's node window in 27 conflict-free offset rounds;
-//   3. the window goes to the grid with one vector atomic per touched node.
+//   2. cell-parallel: the two threads of a cell accumulate its 27-node
+//      stencil (Eqs. 1-4) in registers over all its particles, one thread
+//      the channels (M, MG_x), the other (MG_y, MG_z); each warp (one z layer
+//      of cells) then adds its stencils into its own node slab in 27
+//      warp-synchronous offset rounds;
+//   3. the slabs are summed per node and go to the grid with one vector
+//      atomic per touched node.
 template <int MODE>
-__global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
+__global__ void __launch_bounds__(NT, 4) k_transfer(Dev d, int block_offset)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TransferSmem &sm = *reinterpret_cast<TransferSmem *>(smem_raw);
@@ -413,9 +426,6 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
             sm.tip[0] = S->pose.tip_next[0]; sm.tip[1] = S->pose.tip_next[1]; sm.tip[2] = S->pose.tip_next[2];
         }
     }
-    for (int t = tid; t < GAN; t += NT) {
-        sm.A[0][t] = 0.f; sm.A[1][t] = 0.f; sm.A[2][t] = 0.f; sm.A[3][t] = 0.f;
-    }
     if (tid < NCELL) { sm.ccount[tid] = 0; sm.ccur[tid] = 0; }
     __syncthreads();
     const Inst &I = sm.inst;
@@ -433,7 +443,12 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
     }
     const bool got = count == 0 || mbar_wait_bounded(&sm.bar, 0);
     if (!__syncthreads_and(got)) {
-        if (tid == 0) atomic_or_status(S, ST_TIMEOUT);
+        // the run is reported as failed; before the CTA releases its shared
+        // memory, wait (again bounded) for the copies still in flight
+        if (tid == 0) {
+            atomic_or_status(S, ST_TIMEOUT);
+            mbar_wait_bounded(&sm.bar, 0);
+        }
         return;
     }
 
@@ -534,7 +549,7 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
 #pragma unroll
                         for (int c = 0; c < 3; ++c) sm.P[12 + c][r] = nf[c];
                     } else {
-                        p2g_atomic(sm.A, wx, wy, wz, nw, nf, Q, mv, I.mp);
+                        p2g_global(d.acc, I, nb[0], nb[1], nb[2], nw, nf, Q, mv, I.mp);
                         cl = 255;
                     }
                 }
@@ -602,103 +617,98 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
     }
     __syncthreads();
 
-    // 2. cell-parallel P2G: two threads per cell (adjacent lanes, each half of
-    //    the cell's particles), 27 nodes x 4 channels in registers
+    // 2. cell-parallel P2G: the two threads of a cell (adjacent lanes) each
+    //    take two of the four channels over all the cell's particles; a
+    //    channel's value at node (i, j, k) is w (a + q . d) with (a, q) = (1, 0)
+    //    for M and (m v_r, row r of Q) for MG_r, d = (i - f0, j - f1, k - f2)
     {
-        const int cl = tid >> 1, half = tid & 1;
-        const int clx = cl & 3, cly = (cl >> 2) & 3, clz = cl >> 4;
+        const int cl = tid >> 1, h = tid & 1;
+        const int clx = cl & 3, cly = (cl >> 2) & 3;
         const int ncl = sm.ccount[cl], off = sm.coff[cl];
-        const int my_n = (ncl - half + 1) >> 1;
         const float2 z2 = make_float2(0.f, 0.f);
-        float2 acca[27], accb[27];
+        float2 acc[27];
 #pragma unroll
-        for (int o = 0; o < 27; ++o) { acca[o] = z2; accb[o] = z2; }
-        for (int it = 0; it < my_n; ++it) {
-            const int r = sm.idx[off + half + 2 * it];
-            float Q[9], mv[3], f[3], w[3][3];
-#pragma unroll
-            for (int c = 0; c < 9; ++c) Q[c] = sm.P[c][r];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) mv[c] = sm.P[9 + c][r];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                f[c] = sm.P[12 + c][r];
-                const float a = 1.5f - f[c], bb = f[c] - 1.f, cc = f[c] - 0.5f;
-                w[c][0] = 0.5f * a * a; w[c][1] = 0.75f - bb * bb; w[c][2] = 0.5f * cc * cc;
+        for (int o = 0; o < 27; ++o) acc[o] = z2;
+        const float *rowA1 = sm.P[9 + 2 * h], *rowQ1 = sm.P[6 * h];
+        for (int it = 0; it < ncl; ++it) {
+            const int r = sm.idx[off + it];
+            const float f0 = sm.P[12][r], f1 = sm.P[13][r], f2 = sm.P[14][r];
+            const float a1 = rowA1[r], q10 = rowQ1[r], q11 = rowQ1[CAP + r], q12 = rowQ1[2 * CAP + r];
+            float a0 = 1.f, q00 = 0.f, q01 = 0.f, q02 = 0.f;
+            if (h) { a0 = sm.P[10][r]; q00 = sm.P[3][r]; q01 = sm.P[4][r]; q02 = sm.P[5][r]; }
+            float wx[3], wy[3], wz[3];
+            {
+                float a = 1.5f - f0, bb = f0 - 1.f, cc = f0 - 0.5f;
+                wx[0] = 0.5f * a * a; wx[1] = 0.75f - bb * bb; wx[2] = 0.5f * cc * cc;
+                a = 1.5f - f1; bb = f1 - 1.f; cc = f1 - 0.5f;
+                wy[0] = 0.5f * a * a; wy[1] = 0.75f - bb * bb; wy[2] = 0.5f * cc * cc;
+                a = 1.5f - f2; bb = f2 - 1.f; cc = f2 - 0.5f;
+                wz[0] = 0.5f * a * a; wz[1] = 0.75f - bb * bb; wz[2] = 0.5f * cc * cc;
             }
-            float2 Aa[3], Ab[3], Ya[3], Yb[3], Za[3], Zb[3], wy2[3], wz2[3];
+            // value = w_i w_j w_k (A(i) + Y(j)) + w_i w_j (w_k Z(k)): the x and y
+            // parts ride on the (i, j) product, the z part is folded into H(k)
+            float2 A2[3], Y2[3], H2[3], wz2[3];
 #pragma unroll
             for (int o = 0; o < 3; ++o) {
-                const float d0 = (float)o - f[0], d1 = (float)o - f[1], d2 = (float)o - f[2];
-                Aa[o] = make_float2(1.f, mv[0] + Q[0] * d0);
-                Ab[o] = make_float2(mv[1] + Q[3] * d0, mv[2] + Q[6] * d0);
-                Ya[o] = make_float2(0.f, Q[1] * d1);
-                Yb[o] = make_float2(Q[4] * d1, Q[7] * d1);
-                Za[o] = make_float2(0.f, Q[2] * d2);
-                Zb[o] = make_float2(Q[5] * d2, Q[8] * d2);
-                wy2[o] = dup2(w[1][o]);
-                wz2[o] = dup2(w[2][o]);
+                const float d0 = (float)o - f0, d1 = (float)o - f1, d2 = (float)o - f2;
+                A2[o] = make_float2(fmaf(q00, d0, a0), fmaf(q10, d0, a1));
+                Y2[o] = make_float2(q01 * d1, q11 * d1);
+                H2[o] = make_float2(wz[o] * (q02 * d2), wz[o] * (q12 * d2));
+                wz2[o] = dup2(wz[o]);
             }
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const float2 wx2 = dup2(w[0][i]);
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    const float2 wij = fmul2(wx2, wy2[j]);
-                    const float2 Aij = fadd2(Aa[i], Ya[j]), Bij = fadd2(Ab[i], Yb[j]);
+                    const float2 wij = dup2(wx[i] * wy[j]);
+                    const float2 G = fmul2(wij, fadd2(A2[i], Y2[j]));
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         const int o = (i * 3 + j) * 3 + k;
-                        const float2 w2 = fmul2(wij, wz2[k]);
-                        acca[o] = ffma2(w2, fadd2(Aij, Za[k]), acca[o]);
-                        accb[o] = ffma2(w2, fadd2(Bij, Zb[k]), accb[o]);
+                        acc[o] = ffma2(G, wz2[k], acc[o]);
+                        acc[o] = ffma2(wij, H2[k], acc[o]);
                     }
                 }
-            }
         }
-        // the two lanes of a cell swap halves so that the even lane holds the
-        // cell's (M, MG_x) and the odd lane its (MG_y, MG_z)
-        const float mp = I.mp;
-#pragma unroll
-        for (int o = 0; o < 27; ++o) {
-            const float2 send = half ? acca[o] : accb[o];
-            float2 recv;
-            recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
-            recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
-            if (half) accb[o] = fadd2(accb[o], recv);
-            else acca[o] = fadd2(acca[o], recv);
-        }
-        // add the cell stencils to the block window in 27 offset rounds: within
-        // a round every cell writes a different node, so no atomics are needed
-        // (shared-memory float atomics are a compare-and-swap loop on this GPU)
-        const int ch = half * 2;
-        const bool any = ncl > 0;
+        // every warp has read its particles' rows: the rows now hold the slabs
+        __syncthreads();
+        float *slab = &sm.P[0][0] + (tid >> 5) * SLAB;
+        for (int t = lane; t < SLAB; t += 32) slab[t] = 0.f;
+        __syncwarp();
+        float *ch0 = slab + 2 * h * SLCH, *ch1 = ch0 + SLCH;
+        const float s0 = h ? 1.f : I.mp;              // M was accumulated per unit mass
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
+                    // within a round the 16 cells of the warp write 16 different nodes
                     const int o = (i * 3 + j) * 3 + k;
-                    __syncthreads();
-                    if (any) {
-                        const int n = (clz + 1 + k) * GAZ + (cly + 1 + j) * GA + (clx + 1 + i);
-                        const float2 val = half ? accb[o] : make_float2(acca[o].x * mp, acca[o].y);
-                        sm.A[ch][n] += val.x;
-                        sm.A[ch + 1][n] += val.y;
-                    }
+                    const int n = (k * SLY + cly + j) * SLX + clx + i;
+                    ch0[n] += acc[o].x * s0;
+                    ch1[n] += acc[o].y;
+                    __syncwarp();
                 }
     }
     __syncthreads();
-    // 3. block window -> grid: one vector atomic per touched node
-    for (int t = tid; t < GA * GA * GA; t += NT) {
-        const int lx = t % GA, ly = (t / GA) % GA, lz = t / (GA * GA);
-        const int n = lz * GAZ + ly * GA + lx;
-        const float m = sm.A[0][n];
+    // 3. slabs -> grid: node plane z of the block window gets the slabs of the
+    //    (up to three) cell layers below it; one vector atomic per touched node
+    for (int t = tid; t < (BLK + 2) * (BLK + 2) * (BLK + 2); t += NT) {
+        const int X = t % (BLK + 2), Y = (t / (BLK + 2)) % (BLK + 2), Z = t / ((BLK + 2) * (BLK + 2));
+        float m = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        const int w0 = Z >= 2 ? Z - 2 : 0, w1 = Z < BLK ? Z : BLK - 1;
+        for (int w = w0; w <= w1; ++w) {
+            const float *sl = &sm.P[0][0] + w * SLAB + ((Z - w) * SLY + Y) * SLX + X;
+            m += sl[0];
+            g0 += sl[SLCH];
+            g1 += sl[2 * SLCH];
+            g2 += sl[3 * SLCH];
+        }
         if (m != 0.f) {
-            const int ax = gx0 - 1 + lx, ay = gy0 - 1 + ly, az = gz0 - 1 + lz;
-            if (ax >= 0 && ay >= 0 && az >= 0 && ax < I.nx && ay < I.ny && az < I.nz)
-                atomicAdd(&d.acc[node_of(I, ax, ay, az)], make_float4(m, sm.A[1][n], sm.A[2][n], sm.A[3][n]));
+            const int ax = gx0 + X, ay = gy0 + Y, az = gz0 + Z;
+            if (ax < I.nx && ay < I.ny && az < I.nz)
+                atomicAdd(&d.acc[node_of(I, ax, ay, az)], make_float4(m, g0, g1, g2));
         }
     }
     if (cands) {
