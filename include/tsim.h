@@ -50,7 +50,7 @@ extern "C" {
 #define TSIM_ERR_CUDA 3          /* a CUDA runtime call failed */
 #define TSIM_ERR_NUMERIC 4       /* non-finite state or J <= 0 (latched) */
 #define TSIM_ERR_DOMAIN 5        /* a particle left the node box (latched) */
-#define TSIM_ERR_CAPACITY 6      /* a cell block overflowed its slots (latched) */
+#define TSIM_ERR_CAPACITY 6      /* a full cell block found the instance's spill slots full too (latched) */
 #define TSIM_ERR_STATE 7         /* calls out of order (e.g. step before particles) */
 #define TSIM_ERR_TIMEOUT 8       /* a bounded device wait gave up (latched) */
 
@@ -134,6 +134,9 @@ typedef struct {
     int64_t particle_updates;  /* particles x passes, summed over instances */
     uint32_t status;           /* OR of latched device error bits of all instances */
     int32_t n_inst;
+    int64_t spilled;           /* particles found in spill slots, summed over substeps */
+    int32_t spill_max;         /* most particles one instance held in spill slots at once */
+    int32_t pad_;
 } tsim_stats_t;
 
 /* Create a context of n_inst instances on the current CUDA device.
@@ -221,7 +224,7 @@ int tsim_read_indenter_height(tsim_ctx *ctx, int inst, float *h, int W, int H, f
 int tsim_read_markers(tsim_ctx *ctx, int inst, const int32_t *ids, int m, float *xyz,
                       int on_device);
 
-/* Per-substep log of instance inst for the last n substeps (n <= 4096):
+/* Per-substep log of instance inst for the last n substeps (n <= 32768):
  * passes[n] taken by the relative-rest loop and calib[n] the id of the
  * calibration particle x_e.  Either pointer may be NULL.  Synchronises. */
 int tsim_read_log(tsim_ctx *ctx, int inst, int32_t *passes, int32_t *calib, int n);
@@ -266,11 +269,17 @@ int tsim_autotune(tsim_ctx *ctx, int n_substeps, tsim_tuning_t *out);
  * over relative-rest passes (enable != 0) or launch kernels one by one. */
 int tsim_use_graph(tsim_ctx *ctx, int enable);
 
-/* Per-kernel timing with CUDA events recorded on the context stream around
- * every launch of the fused transfer kernel (enable != 0).
- * tsim_kernel_time returns its launches and total milliseconds since the
- * last reset and resets the counters.  Synchronises. */
+/* Per-kernel timing with CUDA events recorded on the context stream
+ * (enable != 0): around every launch of the commit transfer (the accepted
+ * pass of Algorithm 1 that moves x and F) and around every substep's loop of
+ * repeated passes (transfer, grid update and check of each repeat pass; in
+ * graph mode the events bracket the loop node as a whole).
+ * tsim_pass_time returns, since the last reset, the commit launches, their
+ * total milliseconds and the total milliseconds inside the repeat-pass loops
+ * (any output may be NULL), and resets the counters; tsim_kernel_time returns
+ * the first two.  Both synchronise. */
 int tsim_profile(tsim_ctx *ctx, int enable);
+int tsim_pass_time(tsim_ctx *ctx, int64_t *launches, double *commit_ms, double *loop_ms);
 int tsim_kernel_time(tsim_ctx *ctx, int64_t *launches, double *total_ms);
 
 /* ---- Allocation-free particle-to-grid transfer --------------------------

@@ -3,6 +3,7 @@
 // CUDA graph with a device-driven relative-rest loop) and error latching.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -33,7 +34,9 @@ static int fail(int code, const std::string &msg)
 struct GraphChunk {
     int n = 0;
     cudaGraphExec_t exec = nullptr;
-    std::vector<cudaEvent_t> ev;        // start/stop pairs around the commit transfer
+    // per substep three events: before the relative-rest loop, before the
+    // commit transfer (= after the loop), after the commit transfer
+    std::vector<cudaEvent_t> ev;
     bool pending = false;               // launched, timings not harvested
 };
 
@@ -70,6 +73,7 @@ struct tsim_ctx {
     size_t ev_used = 0;
     long long prof_launches = 0;
     double prof_ms = 0.0;
+    double prof_loop_ms = 0.0;          // time inside the relative-rest loops (repeat passes)
 };
 
 static const int RO_MAX = 1 << 20;
@@ -173,13 +177,19 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
         I.ind_kind = K_NONE;
         I.walls = 1;
         fill_material(I, g, m, 1e-5f);
+        I.spc = (int)std::max(4096ll, (np / 32 + 3) / 4 * 4);
         blocks += I.nblocks;
         long long nn = (long long)g.nx * g.ny * g.nz;
         nodes += nn;
         if (nn > c->max_nodes) c->max_nodes = nn;
         parts += np;
     }
-    if (blocks * (long long)CAP > (1ll << 40) || blocks > (1ll << 30)) {
+    long long spill = 0;
+    for (int i = 0; i < n_inst; ++i) {              // spill slots follow the cell blocks' slots
+        c->hinst[i].sp0 = blocks * (long long)CAP + spill;
+        spill += c->hinst[i].spc;
+    }
+    if (blocks * (long long)CAP + spill > (1ll << 31) || blocks > (1ll << 30)) {
         delete c;
         return fail(TSIM_ERR_INVALID_ARG, "problem too large");
     }
@@ -202,7 +212,7 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
         for (long long a = 0; a < nch; ++a) gch.push_back(make_int2(i, (int)first));
     }
     d.n_gchunk = (long long)gch.size();
-    d.S = blocks * CAP;
+    d.S = blocks * CAP + spill;
     d.n_inst = n_inst;
     const size_t S = (size_t)d.S;
     struct A {
@@ -442,6 +452,7 @@ extern "C" int tsim_write_particles(tsim_ctx *c, int inst, const float *x, const
     CU(cudaMemcpyAsync(d.sF + o * 9, F, sizeof(float) * 9 * n, kind, c->stream));
     CU(cudaMemcpyAsync(d.stag + o, tag, sizeof(uint32_t) * n, kind, c->stream));
     CU(cudaMemsetAsync(d.cnt[c->par_next] + I.block0, 0, sizeof(int) * I.nblocks, c->stream));
+    CU(cudaMemsetAsync(&d.ist[inst].nsp[c->par_next], 0, sizeof(int), c->stream));
     launch_bin_staged(d, inst, n, c->par_next, c->stream);
     CU(cudaGetLastError());
     c->have_particles[inst] = 1;
@@ -459,24 +470,26 @@ static int launch_substeps_stream(tsim_ctx *c, int n)
         launch_round_begin(c->d, c->stream);
         launch_grid(c->d, c->max_nodes, c->grid_threads, c->grid_flat, c->stream);
         launch_check(c->d, 0, 0, c->stream);
-        for (int j = 1; j < limit; ++j) {
-            launch_transfer(c->d, MODE_ITER_, 0, (int)c->total_blocks, c->stream);
-            launch_grid(c->d, c->max_nodes, c->grid_threads, c->grid_flat, c->stream);
-            launch_check(c->d, 0, 0, c->stream);
-        }
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEvent_t ew = nullptr, e0 = nullptr, e1 = nullptr;
         if (c->profile) {
-            if (c->ev_used + 2 > c->ev_pool.size()) {
-                for (int a = 0; a < 256; ++a) {
+            if (c->ev_used + 3 > c->ev_pool.size()) {
+                for (int a = 0; a < 255; ++a) {
                     cudaEvent_t e;
                     CU(cudaEventCreate(&e));
                     c->ev_pool.push_back(e);
                 }
             }
+            ew = c->ev_pool[c->ev_used++];
             e0 = c->ev_pool[c->ev_used++];
             e1 = c->ev_pool[c->ev_used++];
-            CU(cudaEventRecord(e0, c->stream));
+            CU(cudaEventRecord(ew, c->stream));
         }
+        for (int j = 1; j < limit; ++j) {
+            launch_transfer(c->d, MODE_ITER_, 0, (int)c->total_blocks, c->stream);
+            launch_grid(c->d, c->max_nodes, c->grid_threads, c->grid_flat, c->stream);
+            launch_check(c->d, 0, 0, c->stream);
+        }
+        if (c->profile) CU(cudaEventRecord(e0, c->stream));
         launch_transfer(c->d, MODE_COMMIT_, 0, (int)c->total_blocks, c->stream);
         if (c->profile) CU(cudaEventRecord(e1, c->stream));
         CU(cudaGetLastError());
@@ -509,7 +522,7 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
     int zero = 0;
     dim3 grid_grid, grid_blk;
     grid_launch_shape(d, c->max_nodes, c->grid_threads, c->grid_flat, grid_grid, grid_blk);
-    const dim3 tr_grid((unsigned int)c->total_blocks), tr_blk(NT);
+    const dim3 tr_grid((unsigned int)c->total_blocks), tr_blk(NT), sp_grid(SPILL_CTAS);
     cudaGraphNode_t prev = nullptr;
     out.n = n;
     for (auto e : out.ev) cudaEventDestroy(e);
@@ -535,32 +548,51 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
         wp.conditional.handle = h;
         wp.conditional.type = cudaGraphCondTypeWhile;
         wp.conditional.size = 1;
-        CU(cudaGraphAddNode(&n_while, g, &n_chk, nullptr, 1, &wp));
+        // with profiling an event before the loop node (event nodes cannot sit
+        // inside a conditional body, so the loop is timed whole)
+        cudaGraphNode_t while_deps[2] = {n_chk, nullptr};
+        int n_while_deps = 1;
+        cudaEvent_t ew = nullptr, e0 = nullptr, e1 = nullptr;
+        if (c->profile) {
+            CU(cudaEventCreate(&ew));
+            CU(cudaEventCreate(&e0));
+            CU(cudaEventCreate(&e1));
+            out.ev.push_back(ew);
+            out.ev.push_back(e0);
+            out.ev.push_back(e1);
+            CU(cudaGraphAddEventRecordNode(&while_deps[1], g, &n_chk, 1, ew));
+            n_while_deps = 2;
+        }
+        CU(cudaGraphAddNode(&n_while, g, while_deps, nullptr, n_while_deps, &wp));
         cudaGraph_t body = wp.conditional.phGraph_out[0];
-        cudaGraphNode_t b_tr, b_grid, b_chk;
-        rc = add_kernel(body, &b_tr, nullptr, 0, fn_transfer(MODE_ITER_), tr_grid, tr_blk, a_tr, transfer_smem_bytes());
+        cudaGraphNode_t b_tr[2], b_grid, b_chk;
+        // the transfer of the cell blocks and of the spill slots run side by side
+        rc = add_kernel(body, &b_tr[0], nullptr, 0, fn_transfer(MODE_ITER_), tr_grid, tr_blk, a_tr,
+                        transfer_smem_bytes());
         if (rc) break;
-        rc = add_kernel(body, &b_grid, &b_tr, 1, fn_grid(c->grid_flat), grid_grid, grid_blk, a_grid);
+        rc = add_kernel(body, &b_tr[1], nullptr, 0, fn_spill(MODE_ITER_), sp_grid, tr_blk, a_grid);
+        if (rc) break;
+        rc = add_kernel(body, &b_grid, b_tr, 2, fn_grid(c->grid_flat), grid_grid, grid_blk, a_grid);
         if (rc) break;
         rc = add_kernel(body, &b_chk, &b_grid, 1, fn_check(), dim3(1), dim3(256), a_chk);
         if (rc) break;
         cudaGraphNode_t last = n_while;
         if (c->profile) {
-            cudaEvent_t e0, e1;
-            CU(cudaEventCreate(&e0));
-            CU(cudaEventCreate(&e1));
-            out.ev.push_back(e0);
-            out.ev.push_back(e1);
             CU(cudaGraphAddEventRecordNode(&n_ev0, g, &last, 1, e0));
             last = n_ev0;
         }
-        rc = add_kernel(g, &n_commit, &last, 1, fn_transfer(MODE_COMMIT_), tr_grid, tr_blk, a_tr,
+        cudaGraphNode_t n_commits[2];
+        rc = add_kernel(g, &n_commits[0], &last, 1, fn_transfer(MODE_COMMIT_), tr_grid, tr_blk, a_tr,
                         transfer_smem_bytes());
         if (rc) break;
-        prev = n_commit;
+        rc = add_kernel(g, &n_commits[1], &last, 1, fn_spill(MODE_COMMIT_), sp_grid, tr_blk, a_grid);
+        if (rc) break;
         if (c->profile) {
-            CU(cudaGraphAddEventRecordNode(&n_ev1, g, &n_commit, 1, out.ev.back()));
+            CU(cudaGraphAddEventRecordNode(&n_ev1, g, n_commits, 2, out.ev.back()));
             prev = n_ev1;
+        } else {
+            CU(cudaGraphAddEmptyNode(&n_commit, g, n_commits, 2));
+            prev = n_commit;
         }
     }
     if (rc == TSIM_OK) {
@@ -571,29 +603,34 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
     return rc;
 }
 
+// events in triples (loop start, commit start, commit end) per substep
+static int harvest_events(tsim_ctx *c, const std::vector<cudaEvent_t> &ev, size_t n)
+{
+    for (size_t a = 0; a + 3 <= n; a += 3) {
+        CU(cudaEventSynchronize(ev[a + 2]));
+        float ms = 0.f, lms = 0.f;
+        CU(cudaEventElapsedTime(&lms, ev[a], ev[a + 1]));
+        CU(cudaEventElapsedTime(&ms, ev[a + 1], ev[a + 2]));
+        c->prof_ms += ms;
+        c->prof_loop_ms += lms;
+        c->prof_launches += 1;
+    }
+    return TSIM_OK;
+}
+
 static int harvest(tsim_ctx *c, GraphChunk &g)
 {
     if (!g.pending) return TSIM_OK;
-    for (size_t a = 0; a + 1 < g.ev.size(); a += 2) {
-        CU(cudaEventSynchronize(g.ev[a + 1]));
-        float ms = 0.f;
-        CU(cudaEventElapsedTime(&ms, g.ev[a], g.ev[a + 1]));
-        c->prof_ms += ms;
-        c->prof_launches += 1;
-    }
+    int rc = harvest_events(c, g.ev, g.ev.size());
+    if (rc) return rc;
     g.pending = false;
     return TSIM_OK;
 }
 
 static int harvest_stream(tsim_ctx *c)
 {
-    for (size_t a = 0; a + 1 < c->ev_used; a += 2) {
-        CU(cudaEventSynchronize(c->ev_pool[a + 1]));
-        float ms = 0.f;
-        CU(cudaEventElapsedTime(&ms, c->ev_pool[a], c->ev_pool[a + 1]));
-        c->prof_ms += ms;
-        c->prof_launches += 1;
-    }
+    int rc = harvest_events(c, c->ev_pool, c->ev_used);
+    if (rc) return rc;
     c->ev_used = 0;
     return TSIM_OK;
 }
@@ -713,6 +750,8 @@ extern "C" int tsim_stats(tsim_ctx *c, tsim_stats_t *out)
         out->particle_updates += h[i].passes_total * (int64_t)c->hinst[i].n_particles;
         out->status |= h[i].status;
         if (i == 0) out->substeps = h[i].substeps;
+        out->spilled += h[i].spilled;
+        if (h[i].sp_max > out->spill_max) out->spill_max = h[i].sp_max;
     }
     return TSIM_OK;
 }
@@ -731,7 +770,7 @@ extern "C" int tsim_read_particles(tsim_ctx *c, int inst, float *x, float *v, fl
     const Inst &I = c->hinst[inst];
     if (n != I.n_particles) return fail(TSIM_ERR_INVALID_ARG, "n must equal the instance's particle count");
     if (!c->have_particles[inst]) return fail(TSIM_ERR_STATE, "no particles written");
-    launch_gather(c->d, inst, I.nblocks, c->par_next, c->stream);
+    launch_gather(c->d, inst, (long long)I.nblocks * CAP + I.spc, c->par_next, c->stream);
     CU(cudaGetLastError());
     const size_t o = (size_t)I.id0;
     if (x && (rc = copy_out(c, x, c->d.sx + o * 3, sizeof(float) * 3 * n, on_device))) return rc;
@@ -766,7 +805,8 @@ extern "C" int tsim_read_surface(tsim_ctx *c, int inst, float *height, float *no
     const Inst &I = c->hinst[inst];
     const size_t WH = (size_t)W * H;
     float *num = c->ro, *den = c->ro + WH, *h = c->ro + 2 * WH, *nrm = c->ro + 3 * WH;
-    launch_surface(c->d, inst, I.nblocks, c->par_next, num, den, h, nrm, W, H, pitch, I.H, c->stream);
+    launch_surface(c->d, inst, (long long)I.nblocks * CAP + I.spc, c->par_next, num, den, h, nrm, W, H, pitch, I.H,
+                   c->stream);
     CU(cudaGetLastError());
     if (height && (rc = copy_out(c, height, h, sizeof(float) * WH, on_device))) return rc;
     if (normal && (rc = copy_out(c, normal, nrm, sizeof(float) * WH * 3, on_device))) return rc;
@@ -790,7 +830,8 @@ extern "C" int tsim_read_displacement(tsim_ctx *c, int inst, const float *x_ref,
         xr = c->d.sv + (size_t)I.id0 * 3;
     }
     float *acc = c->ro, *uf = c->ro + 4 * WH;
-    launch_surface_disp(c->d, inst, I.nblocks, c->par_next, xr, acc, uf, W, H, pitch, c->stream);
+    launch_surface_disp(c->d, inst, (long long)I.nblocks * CAP + I.spc, c->par_next, xr, acc, uf, W, H, pitch,
+                        c->stream);
     CU(cudaGetLastError());
     rc = copy_out(c, u, uf, sizeof(float) * 3 * WH, on_device);
     if (rc) return rc;
@@ -819,7 +860,7 @@ extern "C" int tsim_read_markers(tsim_ctx *c, int inst, const int32_t *ids, int 
     if (!c->have_particles[inst]) return fail(TSIM_ERR_STATE, "no particles written");
     const Inst &I = c->hinst[inst];
     CU(cudaMemcpyAsync(c->ids, ids, sizeof(int) * m, cudaMemcpyHostToDevice, c->stream));
-    launch_gather(c->d, inst, I.nblocks, c->par_next, c->stream);
+    launch_gather(c->d, inst, (long long)I.nblocks * CAP + I.spc, c->par_next, c->stream);
     launch_pick(c->d, inst, c->ids, m, c->pick, c->stream);
     CU(cudaGetLastError());
     rc = copy_out(c, xyz, c->pick, sizeof(float) * 3 * m, on_device);
@@ -831,7 +872,7 @@ extern "C" int tsim_read_log(tsim_ctx *c, int inst, int32_t *passes, int32_t *ca
 {
     int rc = check_ctx(c, inst);
     if (rc) return rc;
-    if (n < 0 || n > LOGN) return fail(TSIM_ERR_INVALID_ARG, "n must be 0..4096");
+    if (n < 0 || n > LOGN) return fail(TSIM_ERR_INVALID_ARG, "n must be 0..32768");
     CU(cudaStreamSynchronize(c->stream));
     std::vector<int2> lg(LOGN);
     InstState st;
@@ -869,7 +910,7 @@ extern "C" int tsim_profile(tsim_ctx *c, int enable)
     return TSIM_OK;
 }
 
-extern "C" int tsim_kernel_time(tsim_ctx *c, int64_t *launches, double *total_ms)
+extern "C" int tsim_pass_time(tsim_ctx *c, int64_t *launches, double *commit_ms, double *loop_ms)
 {
     int rc = check_ctx(c, 0);
     if (rc) return rc;
@@ -878,10 +919,17 @@ extern "C" int tsim_kernel_time(tsim_ctx *c, int64_t *launches, double *total_ms
         if ((rc = harvest(c, g))) return rc;
     if ((rc = harvest_stream(c))) return rc;
     if (launches) *launches = c->prof_launches;
-    if (total_ms) *total_ms = c->prof_ms;
+    if (commit_ms) *commit_ms = c->prof_ms;
+    if (loop_ms) *loop_ms = c->prof_loop_ms;
     c->prof_launches = 0;
     c->prof_ms = 0.0;
+    c->prof_loop_ms = 0.0;
     return TSIM_OK;
+}
+
+extern "C" int tsim_kernel_time(tsim_ctx *c, int64_t *launches, double *total_ms)
+{
+    return tsim_pass_time(c, launches, total_ms, nullptr);
 }
 
 // ---------------------------------------------------------------- execution configuration

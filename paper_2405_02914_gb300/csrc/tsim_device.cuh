@@ -23,7 +23,8 @@ constexpr int GAZ = 68;              // z stride of the P2G window (64 + 4: conf
 constexpr int GAN = GAZ * GA;        // floats per P2G window channel
 constexpr int NCELL = BLK * BLK * BLK;
 constexpr int MAX_KF = 64;
-constexpr int LOGN = 4096;
+constexpr int SPILL_CTAS = 16;       // extra CTAs of every transfer launch that process the spill slots
+constexpr int LOGN = 32768;           // per-substep log ring (passes, calibration particle) per instance
 
 constexpr uint32_t TAG_BOTTOM = 0x80000000u;
 constexpr uint32_t TAG_TOP = 0x40000000u;
@@ -49,6 +50,8 @@ struct Inst {                      // per-instance constants
     float ip[8];
     float fric, tip_offset;
     int nkf;
+    int spc;                       // spill slots of this instance (particles beyond a full cell block)
+    long long sp0;                 // first spill slot
 };
 
 struct Pose {
@@ -69,6 +72,10 @@ struct InstState {                 // mutable per instance
     int dirty;
     long long passes_total;
     long long substeps;
+    int nsp[2];                    // particles in the spill slots, per parity
+    int sp_max;                    // most particles held in the spill slots at one time
+    int pad_;
+    long long spilled;             // spill-slot particles summed over committed substeps
 };
 
 struct Global {
@@ -99,6 +106,20 @@ struct Dev {                       // device pointers (passed by value to kernel
     long long n_gchunk;
     int n_inst;
 };
+
+// Slot of the t-th particle position of instance I in parity par: t < nblocks *
+// CAP walks the cell blocks' slots, the rest the instance's spill slots; -1
+// where that position holds no particle.
+__device__ __forceinline__ long long inst_slot(const Dev &d, const Inst &I, int inst, int par, long long t)
+{
+    const long long nb = (long long)I.nblocks * CAP;
+    if (t < nb) {
+        const int b = I.block0 + (int)(t / CAP), r = (int)(t % CAP);
+        return r < min(d.cnt[par][b], CAP) ? (long long)b * CAP + r : -1;
+    }
+    const long long sp = t - nb;
+    return sp < min(d.ist[inst].nsp[par], I.spc) ? I.sp0 + sp : -1;
+}
 
 // ----------------------------------------------------------------- B-spline
 

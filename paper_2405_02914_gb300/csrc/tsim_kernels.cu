@@ -49,6 +49,11 @@ __global__ void k_round_begin(Dev d)
     S->pose = P;
     S->phase = 0;
     S->pass = 0;
+    // the commit of this substep fills the other parity's spill slots afresh
+    const int nsp = min(S->nsp[par], I.spc);
+    S->spilled += nsp;
+    if (nsp > S->sp_max) S->sp_max = nsp;
+    S->nsp[par ^ 1] = 0;
     const unsigned long long key = S->e_key;
     S->e_key = ~0ull;                              // the commit of this substep fills it again
     if (key == ~0ull) {
@@ -214,7 +219,8 @@ __global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle
 
 enum { MODE_PROLOGUE = 0, MODE_ITER = 1, MODE_COMMIT = 2 };
 
-// Shared memory of one cell block (dynamic, ~53 KB: four CTAs per SM).
+// Shared memory of one cell block (dynamic, ~53 KB: four CTAs fit an SM;
+// the commit variant's registers allow three, the others' four).
 struct TransferSmem {
     // staged x (0..2), F (3..11) and tag bits (12) of the block's particles (TMA);
     // phase 1 overwrites a particle's entries with its P2G coefficients:
@@ -361,6 +367,163 @@ __device__ __noinline__ void p2g_global(float4 *acc, const Inst &I, int bx, int 
             }
 }
 
+// Claim a destination slot for a particle moving into cell block key: the
+// block's next slot, or, when the block is full, the next spill slot of the
+// instance (-1 when those are full too).
+__device__ __forceinline__ long long claim_spill(const Dev &d, const Inst &I, int inst, int dpar)
+{
+    const int sp = atomicAdd(&d.ist[inst].nsp[dpar], 1);
+    return sp < I.spc ? I.sp0 + sp : -1;
+}
+
+// One particle held in a spill slot, through the same pass as the particles
+// of the cell blocks (Eqs. 1-9): G2P from the grid, the move on a commit
+// pass, stress, P2G with global atomics, re-binning, candidate key.
+template <int MODE>
+__device__ void spill_particle(const Dev &d, const Inst &I, InstState *S, int inst, int par, long long slot)
+{
+    const long long SS = d.S;
+    const float *src = d.P[par];
+    float x[3], F[9], v[3], C[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[c] = src[c * SS + slot];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) F[c] = src[(3 + c) * SS + slot];
+    const uint32_t tag = d.T[par][slot];
+    int base[3];
+    float f[3], w[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) bspline(x[a], I.inv_dx, base[a], f[a], w[a]);
+    const int ax0 = base[0] + I.ox, ay0 = base[1] + I.oy, az0 = base[2] + I.oz;
+    if (ax0 < 0 || ay0 < 0 || az0 < 0 || ax0 + 2 >= I.nx || ay0 + 2 >= I.ny || az0 + 2 >= I.nz) {
+        atomicOr(&S->status, ST_DOMAIN);
+        return;
+    }
+    if (MODE == MODE_PROLOGUE) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = d.VC[c * SS + slot];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) C[c] = d.VC[(3 + c) * SS + slot];
+    } else {
+        // v = sum w V (Eq. 6), C = 4/dx^2 sum w V (x_i - x_p)^T (Eq. 7), d in cells
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) C[c] = 0.f;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    const float4 V = d.vel[node_of(I, ax0 + i, ay0 + j, az0 + k)];
+                    const float wt = w[0][i] * w[1][j] * w[2][k];
+                    const float dd[3] = {(float)i - f[0], (float)j - f[1], (float)k - f[2]};
+                    const float Vr[3] = {V.x, V.y, V.z};
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        v[r] += wt * Vr[r];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) C[r * 3 + c] += wt * Vr[r] * dd[c];
+                    }
+                }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) C[c] *= 4.f * I.inv_dx;
+        if ((tag & TAG_BOTTOM) && I.base_mode != BASE_FREE) v[2] = 0.f;   // Algorithm 1
+    }
+    if (MODE == MODE_COMMIT) {
+        float Fn[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                Fn[r * 3 + c] = F[r * 3 + c] + I.dt * (C[r * 3] * F[c] + C[r * 3 + 1] * F[3 + c] + C[r * 3 + 2] * F[6 + c]);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) F[c] = Fn[c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) x[c] += I.dt * v[c];
+    }
+    float tau[9];
+    const float J = kirchhoff(F, I.mu, I.lam, tau);
+    if (!(J > 0.f) || !isfinite(J) || !isfinite(x[0]) || !isfinite(x[1]) || !isfinite(x[2])) {
+        atomicOr(&S->status, ST_NUMERIC);
+        return;
+    }
+    int nb[3];
+    float nf[3], nw[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) bspline(x[a], I.inv_dx, nb[a], nf[a], nw[a]);
+    nb[0] += I.ox; nb[1] += I.oy; nb[2] += I.oz;
+    if (nb[0] < 0 || nb[1] < 0 || nb[2] < 0 || nb[0] + 2 >= I.nx || nb[1] + 2 >= I.ny || nb[2] + 2 >= I.nz) {
+        atomicOr(&S->status, ST_DOMAIN);
+        return;
+    }
+    float Q[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) Q[c] = (I.mp * C[c] + I.kME * tau[c]) * I.dx;
+    const float mv[3] = {I.mp * v[0], I.mp * v[1], I.mp * v[2]};
+    p2g_global(d.acc, I, nb[0], nb[1], nb[2], nw, nf, Q, mv, I.mp);
+    long long cand = slot;
+    if (MODE == MODE_COMMIT) {
+        const int key = I.block0 + ((nb[2] / BLK) * I.nby + (nb[1] / BLK)) * I.nbx + (nb[0] / BLK);
+        const int rr = atomicAdd(&d.cnt[par ^ 1][key], 1);
+        const long long ds = rr < CAP ? (long long)key * CAP + rr : claim_spill(d, I, inst, par ^ 1);
+        if (ds < 0) {
+            atomicOr(&S->status, ST_CAPACITY);
+            return;
+        }
+        float *dst = d.P[par ^ 1];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dst[c * SS + ds] = x[c];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) dst[(3 + c) * SS + ds] = F[c];
+        d.T[par ^ 1][ds] = tag;
+        if (d.G->k_cur + 1 == d.G->k_end) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) d.VC[c * SS + ds] = v[c];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) d.VC[(3 + c) * SS + ds] = C[c];
+        }
+        cand = ds;
+    }
+    if (MODE != MODE_ITER) {
+        float tip[3];
+        if (MODE == MODE_PROLOGUE) {
+            double t4[4], v4[4];
+            pose_tip(d.kf + (long long)inst * MAX_KF * 5, I.nkf, d.G->k_next, t4, v4, (double)I.dt);
+            tip[0] = (float)t4[0]; tip[1] = (float)t4[1]; tip[2] = (float)t4[2];
+        } else {
+            tip[0] = S->pose.tip_next[0]; tip[1] = S->pose.tip_next[1]; tip[2] = S->pose.tip_next[2];
+        }
+        const float e0 = x[0] - tip[0], e1 = x[1] - tip[1], e2 = x[2] - tip[2];
+        const float dd = e0 * e0 + e1 * e1 + e2 * e2;
+        const unsigned long long kk = ((unsigned long long)__float_as_uint(dd) << 32) | (unsigned int)cand;
+        if (kk < *((volatile unsigned long long *)&S->e_key)) atomicMin(&S->e_key, kk);
+    }
+}
+
+// Companion of every transfer launch (SPILL_CTAS CTAs of NT threads): the
+// spill slots of every instance taking part in the pass, grid-strided.
+template <int MODE>
+__global__ void __launch_bounds__(NT) k_spill(Dev d)
+{
+    const int c = blockIdx.x;
+    for (int inst = 0; inst < d.n_inst; ++inst) {
+        InstState *S = d.ist + inst;
+        int par;
+        if (MODE == MODE_PROLOGUE) {
+            if (!S->dirty) continue;
+            par = d.G->par_next;
+        } else {
+            const int ph = S->phase;
+            if (MODE == MODE_ITER && ph != 0) continue;
+            if (MODE == MODE_COMMIT && ph != 1) continue;
+            par = d.G->par_cur;
+        }
+        const Inst &I = d.inst[inst];
+        const int nsp = min(S->nsp[par], I.spc);
+        for (int sp = c * NT + (int)threadIdx.x; sp < nsp; sp += SPILL_CTAS * NT)
+            spill_particle<MODE>(d, I, S, inst, par, I.sp0 + sp);
+    }
+}
+
 // One CTA per cell block of 4x4x4 cells:
 //   0. bulk-copy the block's x, F and tags into shared memory (TMA);
 //   1. particle-parallel: G2P from the shared velocity window (Eqs. 6-7), the
@@ -376,7 +539,7 @@ __device__ __noinline__ void p2g_global(float4 *acc, const Inst &I, int bx, int 
 //   3. the slabs are summed per node and go to the grid with one vector
 //      atomic per touched node.
 template <int MODE>
-__global__ void __launch_bounds__(NT, 4) k_transfer(Dev d, int block_offset)
+__global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TransferSmem &sm = *reinterpret_cast<TransferSmem *>(smem_raw);
@@ -467,16 +630,11 @@ __global__ void __launch_bounds__(NT, 4) k_transfer(Dev d, int block_offset)
         uint32_t tag = 0;
         int cl = 255;
         if (valid) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) x[c] = sm.P[c][r];
-#pragma unroll
-            for (int c = 0; c < 9; ++c) F[c] = sm.P[3 + c][r];
-            tag = __float_as_uint(sm.P[12][r]);
             float f[3], w[3][3];
             int bx, by, bz;
-            bspline(x[0], inv_dx, bx, f[0], w[0]);
-            bspline(x[1], inv_dx, by, f[1], w[1]);
-            bspline(x[2], inv_dx, bz, f[2], w[2]);
+            bspline(sm.P[0][r], inv_dx, bx, f[0], w[0]);
+            bspline(sm.P[1][r], inv_dx, by, f[1], w[1]);
+            bspline(sm.P[2][r], inv_dx, bz, f[2], w[2]);
             const int lx = bx + I.ox - gx0, ly = by + I.oy - gy0, lz = bz + I.oz - gz0;
             if (lx < 0 || ly < 0 || lz < 0 || lx >= BLK || ly >= BLK || lz >= BLK) {
                 err |= ST_DOMAIN;
@@ -495,9 +653,19 @@ __global__ void __launch_bounds__(NT, 4) k_transfer(Dev d, int block_offset)
                     const float s4 = 4.f * inv_dx;   // (4/dx^2) * dx: d above is in cells
 #pragma unroll
                     for (int c = 0; c < 9; ++c) C[c] *= s4;
-                    if ((tag & TAG_BOTTOM) && I.base_mode != BASE_FREE) v[2] = 0.f;   // Algorithm 1
                 }
             }
+        }
+        // x, F and the tag are read from shared memory only now, so that they
+        // are not held in registers across the G2P
+        asm volatile("" ::: "memory");
+        if (valid) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x[c] = sm.P[c][r];
+#pragma unroll
+            for (int c = 0; c < 9; ++c) F[c] = sm.P[3 + c][r];
+            tag = __float_as_uint(sm.P[12][r]);
+            if (MODE != MODE_PROLOGUE && (tag & TAG_BOTTOM) && I.base_mode != BASE_FREE) v[2] = 0.f;   // Algorithm 1
         }
         if (valid && moves) {
             // F <- (I + dt C) F (Eq. 8); x <- x + dt v (Eq. 9)
@@ -570,10 +738,11 @@ __global__ void __launch_bounds__(NT, 4) k_transfer(Dev d, int block_offset)
             basepos = __shfl_sync(0xffffffffu, basepos, leader);
             if (valid) {
                 const int rr = basepos + rank;
-                if (rr >= CAP) {
+                // a full block sends the particle to its instance's spill slots
+                const long long ds = rr < CAP ? (long long)key * CAP + rr : claim_spill(d, I, inst, par ^ 1);
+                if (ds < 0) {
                     err |= ST_CAPACITY;
                 } else {
-                    const long long ds = (long long)key * CAP + rr;
                     cand_slot = ds;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) dst[c * SS + ds] = x[c];
@@ -759,11 +928,12 @@ __global__ void k_bin_staged(Dev d, int inst, int par)
     }
     const int blk = I.block0 + ((ab[2] / BLK) * I.nby + ab[1] / BLK) * I.nbx + ab[0] / BLK;
     const int r = atomicAdd(&d.cnt[par][blk], 1);
-    if (r >= CAP) {
+    const long long slot = r < CAP ? (long long)blk * CAP + r : claim_spill(d, I, inst, par);
+    if (slot < 0) {
         atomic_or_status(d.ist + inst, ST_CAPACITY);
         return;
     }
-    const long long SS = d.S, slot = (long long)blk * CAP + r;
+    const long long SS = d.S;
     float *P = d.P[par];
 #pragma unroll
     for (int c = 0; c < 3; ++c) P[c * SS + slot] = x[c];
@@ -780,10 +950,10 @@ __global__ void k_gather(Dev d, int inst, int par)
 {
     const Inst &I = d.inst[inst];
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)I.nblocks * CAP) return;
-    const int b = I.block0 + (int)(t / CAP), r = (int)(t % CAP);
-    if (r >= d.cnt[par][b]) return;
-    const long long SS = d.S, slot = (long long)b * CAP + r;
+    if (t >= (long long)I.nblocks * CAP + I.spc) return;
+    const long long slot = inst_slot(d, I, inst, par, t);
+    if (slot < 0) return;
+    const long long SS = d.S;
     const uint32_t tag = d.T[par][slot];
     const uint32_t id = tag & ID_MASK;
     if (id >= (uint32_t)I.n_particles) {
@@ -834,10 +1004,10 @@ __global__ void k_surface_splat(Dev d, int inst, int par, float *num, float *den
 {
     const Inst &I = d.inst[inst];
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)I.nblocks * CAP) return;
-    const int b = I.block0 + (int)(t / CAP), r = (int)(t % CAP);
-    if (r >= d.cnt[par][b]) return;
-    const long long SS = d.S, slot = (long long)b * CAP + r;
+    if (t >= (long long)I.nblocks * CAP + I.spc) return;
+    const long long slot = inst_slot(d, I, inst, par, t);
+    if (slot < 0) return;
+    const long long SS = d.S;
     if (!(d.T[par][slot] & TAG_TOP)) return;
     const float *P = d.P[par];
     const float x = P[slot], y = P[SS + slot], z = P[2 * SS + slot];
@@ -885,10 +1055,10 @@ __global__ void k_surface_disp(Dev d, int inst, int par, const float *__restrict
 {
     const Inst &I = d.inst[inst];
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)I.nblocks * CAP) return;
-    const int b = I.block0 + (int)(t / CAP), r = (int)(t % CAP);
-    if (r >= min(d.cnt[par][b], CAP)) return;
-    const long long SS = d.S, slot = (long long)b * CAP + r;
+    if (t >= (long long)I.nblocks * CAP + I.spc) return;
+    const long long slot = inst_slot(d, I, inst, par, t);
+    if (slot < 0) return;
+    const long long SS = d.S;
     const uint32_t tag = d.T[par][slot];
     if (!(tag & TAG_TOP)) return;
     const uint32_t id = tag & ID_MASK;
@@ -996,9 +1166,16 @@ void launch_transfer(const Dev &d, int mode, int block_offset, int nblocks, cuda
 {
     if (nblocks <= 0) return;
     const size_t sh = sizeof(TransferSmem);
-    if (mode == MODE_PROLOGUE) k_transfer<MODE_PROLOGUE><<<nblocks, NT, sh, s>>>(d, block_offset);
-    else if (mode == MODE_ITER) k_transfer<MODE_ITER><<<nblocks, NT, sh, s>>>(d, block_offset);
-    else k_transfer<MODE_COMMIT><<<nblocks, NT, sh, s>>>(d, block_offset);
+    if (mode == MODE_PROLOGUE) {
+        k_transfer<MODE_PROLOGUE><<<nblocks, NT, sh, s>>>(d, block_offset);
+        k_spill<MODE_PROLOGUE><<<SPILL_CTAS, NT, 0, s>>>(d);
+    } else if (mode == MODE_ITER) {
+        k_transfer<MODE_ITER><<<nblocks, NT, sh, s>>>(d, block_offset);
+        k_spill<MODE_ITER><<<SPILL_CTAS, NT, 0, s>>>(d);
+    } else {
+        k_transfer<MODE_COMMIT><<<nblocks, NT, sh, s>>>(d, block_offset);
+        k_spill<MODE_COMMIT><<<SPILL_CTAS, NT, 0, s>>>(d);
+    }
 }
 
 void launch_bin_staged(const Dev &d, int inst, int n, int par, cudaStream_t s)
@@ -1006,9 +1183,9 @@ void launch_bin_staged(const Dev &d, int inst, int n, int par, cudaStream_t s)
     k_bin_staged<<<cdiv(n, 256), 256, 0, s>>>(d, inst, par);
 }
 
-void launch_gather(const Dev &d, int inst, int nblocks, int par, cudaStream_t s)
+void launch_gather(const Dev &d, int inst, long long positions, int par, cudaStream_t s)
 {
-    k_gather<<<cdiv((long long)nblocks * CAP, 256), 256, 0, s>>>(d, inst, par);
+    k_gather<<<cdiv(positions, 256), 256, 0, s>>>(d, inst, par);
 }
 
 void launch_pick(const Dev &d, int inst, const int *ids, int m, float *out, cudaStream_t s)
@@ -1016,22 +1193,21 @@ void launch_pick(const Dev &d, int inst, const int *ids, int m, float *out, cuda
     k_pick<<<cdiv(m, 128), 128, 0, s>>>(d, inst, ids, m, out);
 }
 
-void launch_surface(const Dev &d, int inst, int nblocks, int par, float *num, float *den, float *h,
+void launch_surface(const Dev &d, int inst, long long positions, int par, float *num, float *den, float *h,
                     float *nrm, int W, int H, float pitch, float h_empty, cudaStream_t s)
 {
     cudaMemsetAsync(num, 0, sizeof(float) * (size_t)W * H, s);
     cudaMemsetAsync(den, 0, sizeof(float) * (size_t)W * H, s);
-    k_surface_splat<<<cdiv((long long)nblocks * CAP, 256), 256, 0, s>>>(d, inst, par, num, den, W, H,
-                                                                          1.f / pitch);
+    k_surface_splat<<<cdiv(positions, 256), 256, 0, s>>>(d, inst, par, num, den, W, H, 1.f / pitch);
     k_surface_height<<<cdiv((long long)W * H, 256), 256, 0, s>>>(num, den, h, W * H, h_empty);
     k_surface_normal<<<cdiv((long long)W * H, 256), 256, 0, s>>>(h, nrm, W, H, pitch);
 }
 
-void launch_surface_disp(const Dev &d, int inst, int nblocks, int par, const float *xref, float *acc, float *u,
-                         int W, int H, float pitch, cudaStream_t s)
+void launch_surface_disp(const Dev &d, int inst, long long positions, int par, const float *xref, float *acc,
+                         float *u, int W, int H, float pitch, cudaStream_t s)
 {
     cudaMemsetAsync(acc, 0, sizeof(float) * 4 * (size_t)W * H, s);
-    k_surface_disp<<<cdiv((long long)nblocks * CAP, 256), 256, 0, s>>>(d, inst, par, xref, acc, W, H, 1.f / pitch);
+    k_surface_disp<<<cdiv(positions, 256), 256, 0, s>>>(d, inst, par, xref, acc, W, H, 1.f / pitch);
     k_surface_disp_finish<<<cdiv((long long)W * H, 256), 256, 0, s>>>(acc, u, W * H);
 }
 
@@ -1049,6 +1225,12 @@ void *fn_transfer(int mode)
     if (mode == MODE_PROLOGUE) return (void *)k_transfer<MODE_PROLOGUE>;
     if (mode == MODE_ITER) return (void *)k_transfer<MODE_ITER>;
     return (void *)k_transfer<MODE_COMMIT>;
+}
+void *fn_spill(int mode)
+{
+    if (mode == MODE_PROLOGUE) return (void *)k_spill<MODE_PROLOGUE>;
+    if (mode == MODE_ITER) return (void *)k_spill<MODE_ITER>;
+    return (void *)k_spill<MODE_COMMIT>;
 }
 
 }  // namespace tsim

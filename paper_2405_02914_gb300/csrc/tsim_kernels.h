@@ -15,13 +15,13 @@ void launch_grid(const Dev &d, long long max_nodes, int threads, int flat, cudaS
 void launch_check(const Dev &d, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
 void launch_transfer(const Dev &d, int mode, int block_offset, int nblocks, cudaStream_t s);
 void launch_bin_staged(const Dev &d, int inst, int n, int par, cudaStream_t s);
-void launch_gather(const Dev &d, int inst, int nblocks, int par, cudaStream_t s);
+void launch_gather(const Dev &d, int inst, long long positions, int par, cudaStream_t s);
 void launch_pick(const Dev &d, int inst, const int *ids, int m, float *out, cudaStream_t s);
-void launch_surface(const Dev &d, int inst, int nblocks, int par, float *num, float *den, float *h,
+void launch_surface(const Dev &d, int inst, long long positions, int par, float *num, float *den, float *h,
                     float *nrm, int W, int H, float pitch, float h_empty, cudaStream_t s);
 
-void launch_surface_disp(const Dev &d, int inst, int nblocks, int par, const float *xref, float *acc, float *u,
-                         int W, int H, float pitch, cudaStream_t s);
+void launch_surface_disp(const Dev &d, int inst, long long positions, int par, const float *xref, float *acc,
+                         float *u, int W, int H, float pitch, cudaStream_t s);
 void launch_indenter_height(const Dev &d, int inst, float *h, int W, int H, float pitch, float clip, cudaStream_t s);
 cudaError_t setup_kernels();
 size_t transfer_smem_bytes();
@@ -30,5 +30,6 @@ void *fn_round_begin();
 void *fn_grid(int flat);
 void *fn_check();
 void *fn_transfer(int mode);
+void *fn_spill(int mode);
 
 }  // namespace tsim

@@ -302,6 +302,21 @@ def serve_summary(err, ind, threshold: float = 0.02):
                 p90_err=float(np.percentile(err, 90)), max_served_err=float(served.max()))
 
 
+def served_seconds(fallback, traj, substep, every: int, surr_fps: float, mpm_fps: float) -> float:
+    """Time to serve all frames when the flagged ones fall back to IMPM: every
+    frame pays its network inference (1/surr_fps), and a trajectory with a
+    fallback frame pays IMPM for its whole prefix up to its last flagged
+    frame ((substep / every) frames at 1/mpm_fps each; earlier flagged frames
+    of the same trajectory come out of that run)."""
+    fallback = np.asarray(fallback, bool)
+    traj = np.asarray(traj)
+    frames = np.asarray(substep) // every
+    t = fallback.size / surr_fps
+    for j in np.unique(traj[fallback]):
+        t += frames[fallback & (traj == j)].max() / mpm_fps
+    return float(t)
+
+
 def time_inference(params, P: int = 128, batch: int = 256, reps: int = 20, warmup: int = 3, seed: int = 0):
     """Seconds per batch of the network forward on device-resident inputs
     (CUDA events on the launching stream)."""

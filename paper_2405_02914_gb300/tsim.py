@@ -23,7 +23,7 @@ ERRORS = {1: "TSIM_ERR_INVALID_ARG", 2: "TSIM_ERR_OOM", 3: "TSIM_ERR_CUDA", 4: "
 EXPORTS = ["tsim_create", "tsim_set_solver", "tsim_set_indenter", "tsim_set_trajectory",
            "tsim_write_particles", "tsim_set_substep", "tsim_step", "tsim_read_particles",
            "tsim_read_grid", "tsim_read_surface", "tsim_read_markers", "tsim_read_log", "tsim_sync",
-           "tsim_stats", "tsim_use_graph", "tsim_profile", "tsim_kernel_time", "tsim_last_error",
+           "tsim_stats", "tsim_use_graph", "tsim_profile", "tsim_kernel_time", "tsim_pass_time", "tsim_last_error",
            "tsim_destroy", "tsim_p2g_noalloc", "tsim_read_displacement", "tsim_read_indenter_height",
            "tsim_set_tuning", "tsim_get_tuning", "tsim_autotune"]
 
@@ -60,7 +60,8 @@ class SolverDesc(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("substeps", C.c_int64), ("passes", C.c_int64), ("particle_updates", C.c_int64),
-                ("status", C.c_uint32), ("n_inst", C.c_int32)]
+                ("status", C.c_uint32), ("n_inst", C.c_int32), ("spilled", C.c_int64), ("spill_max", C.c_int32),
+                ("pad_", C.c_int32)]
 
 
 class Tuning(C.Structure):
@@ -103,6 +104,7 @@ def load():
             "tsim_use_graph": (C.c_int, [vp, C.c_int]),
             "tsim_profile": (C.c_int, [vp, C.c_int]),
             "tsim_kernel_time": (C.c_int, [vp, P(C.c_int64), P(C.c_double)]),
+            "tsim_pass_time": (C.c_int, [vp, P(C.c_int64), P(C.c_double), P(C.c_double)]),
             "tsim_last_error": (C.c_char_p, []),
             "tsim_destroy": (None, [vp]),
             "tsim_p2g_noalloc": (C.c_int, [P(GelDesc), P(MaterialDesc), C.c_float, vp, vp, vp, vp, C.c_int,
@@ -333,6 +335,15 @@ def tsim_kernel_time(ctx):
     ms = C.c_double()
     _check(load().tsim_kernel_time(ctx, C.byref(n), C.byref(ms)))
     return n.value, ms.value
+
+
+def tsim_pass_time(ctx):
+    """(commit launches, commit ms, repeat-pass loop ms) since the last reset."""
+    n = C.c_int64()
+    ms = C.c_double()
+    lms = C.c_double()
+    _check(load().tsim_pass_time(ctx, C.byref(n), C.byref(ms), C.byref(lms)))
+    return n.value, ms.value, lms.value
 
 
 def tsim_set_tuning(ctx, grid_threads=256, grid_flat=0, graph_chunk=20):

@@ -68,7 +68,7 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch, capsys):
 
 
 def test_reference_arm_line_carries_the_contract_keys(monkeypatch, capsys):
-    """The reference arm (the FP64 oracle on the host cores) prints one JSON
+    """The reference arm (the FP64 oracle on all host cores) prints one JSON
     line with the same metric and unit as the GPU arm, its own cpu_baseline
     and an e2e object without host-device traffic."""
     import json
@@ -86,7 +86,18 @@ def test_reference_arm_line_carries_the_contract_keys(monkeypatch, capsys):
         assert k in d, k
     assert d["impl"] == "reference" and d["metric"] == b.METRIC and d["unit"] == b.UNIT
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    import oracle as O
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == O.threads()
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_phases_of_the_press_slip_rotate_trajectory():
+    """The bench splits its timed frames by the trajectory's phases, read
+    from the keyframes (press 5000, slip 7500, rotate 7500 substeps)."""
+    from paper_2405_02914_gb300 import inputs as I
+    b = _bench()
+    ph = b._phases(I.scene_pad4m().keyframes)
+    assert ph[:3] == [("press", 0, 5000), ("slip", 5000, 12500), ("rotate", 12500, 20000)]
+    assert ph[3][0] == "hold" and ph[3][1] == 20000

@@ -7,6 +7,7 @@ inputs; the oracle never sees a value produced by the CUDA path except where
 a test hands both sides the *same* snapshot (one-step and sampled checks).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -105,7 +106,7 @@ def test_one_step_matches_oracle_in_contact():
     assert nc > 0 and passes == gp[0]
     dx = sc.gel.dx
     assert np.abs(x - st.x).max() < 1e-4 * dx
-    assert np.abs(v - st.v).max() < 1e-3 * np.abs(st.v).max()
+    assert np.abs(v - st.v).max() < 1e-4 * np.abs(st.v).max()
     assert np.abs(F - st.F).max() < 1e-5
 
 
@@ -167,6 +168,47 @@ def test_slip_rotate_impm_matches_oracle():
     agree = float(np.mean(gp == pl))
     assert agree > 0.98, (agree, np.nonzero(gp != pl))
     assert np.abs(x - st.x).max() < POS_TOL * sc.gel.dx
+
+
+ROT_POS_TOL = 5e-3      # max |dx| / dx after 10,000 substeps with a full 30-degree sticking rotation
+ROT_RMS_TOL = 2e-3      # RMS |dx| / dx, same run
+
+
+def test_c2_speed_full_rotation_matches_oracle():
+    """The loading of the 4.2M-particle pad (dx = 0.3125 mm, dt = 5e-6 s,
+    press at 0.04 m/s, slip at 0.08 m/s, a full 30-degree turn over 7,500
+    substeps at mu = 0.5) on a 16 x 16 x 4-cell gel, GPU against the oracle
+    over the whole trajectory.  Pass counts must agree on >= 98 % of
+    substeps.  Positions: the FP32 path and the FP64 oracle differ by
+    rounding each substep (3e-6 dx on one substep of the full-size pad);
+    once the indenter slides, nearly every substep takes LIMIT passes, and
+    each repeat pass re-applies the stress impulse to the latest velocity,
+    which amplifies those differences.  Measured on GB300: 1.1e-4 dx after
+    the press, 2.0e-4 dx after the slip, 3.4e-3 dx (RMS 1.2e-3 dx) after the
+    turn; the bounds are 1e-3 dx to the end of the slip and ROT_POS_TOL /
+    ROT_RMS_TOL after the turn."""
+    dt, dx = 5e-6, 0.3125e-3
+    n_press, n_slip, n_rot = 1000, 1500, 7500
+    sc = I.scene_small(cx=16, cy=16, cz=4, dx=dx, dt=dt, n_press=n_press, press=0.04 * n_press * dt,
+                       slip=0.08 * n_slip * dt, n_slip=n_slip, rotate=math.radians(30.0), n_rot=n_rot, mu=0.5)
+    state = _init(sc)
+    sim = T.Sim(sc, use_graph=True, states=[state])
+    st, s, ind = _oracle(sc, state)
+    k, agree = 0, []
+    for end, tol in ((n_press + n_slip, POS_TOL), (n_press + n_slip + n_rot, ROT_POS_TOL)):
+        sim.step(end - k)
+        pl, _ = O.run_par(s, ind, sc.keyframes, k, end - k, st)
+        gp, _ = sim.log(end - k)
+        agree.append(gp == pl)
+        x, _, _, _ = sim.particles()
+        d = np.abs(x - st.x) / sc.gel.dx
+        print("substep %d: max %.3g dx, rms %.3g dx" % (end, d.max(), np.sqrt((d ** 2).sum(1).mean())))
+        assert d.max() < tol, (end, d.max())
+        k = end
+    sim.close()
+    assert np.sqrt((d ** 2).sum(1).mean()) < ROT_RMS_TOL
+    assert float(np.mean(np.concatenate(agree))) >= 0.98
+    assert pl.mean() > 4                               # the loop repeats passes through the turn
 
 
 @pytest.mark.parametrize("kind", [I.CYLINDER, I.BOX, I.PRISM, I.PERLIN])
@@ -256,9 +298,11 @@ def test_errors_are_latched_not_faults():
     with pytest.raises(T.TsimError) as e:
         T.Sim(sc, states=[(bad, v, C, F, tag)])
     assert e.value.code == 5
-    big = I.scene_small(cx=8, cy=8, cz=4, kind=I.NONE)
+    # every particle in one cell block: 768 slots there and 4096 spill slots
+    # (the instance's minimum) hold 4864 of these 8192 particles
+    big = I.scene_small(cx=16, cy=16, cz=4, kind=I.NONE)
     xb, vb, Cb, Fb, tb = _init(big)
-    crowd = np.tile(xb[:1], (xb.shape[0], 1))                # every particle in one cell block
+    crowd = np.tile(xb[:1], (xb.shape[0], 1))
     with pytest.raises(T.TsimError) as e:
         T.Sim(big, states=[(crowd, vb, Cb, Fb, tb)])
     assert e.value.code == 6
@@ -266,6 +310,43 @@ def test_errors_are_latched_not_faults():
     nan[0, 0] = np.nan
     with pytest.raises(T.TsimError):
         T.Sim(sc, states=[(nan, v, C, F, tag)])
+
+
+def test_overflowing_blocks_spill_and_match_oracle():
+    """Cell blocks hold 768 slots; a block that receives more sends the rest
+    to its instance's spill slots, which a companion kernel advances through
+    the same pass.  An 8 x 8 x 8-cell gel squeezed into half its height
+    (F = diag(1, 1, 0.5), so J = 0.5) starts with up to 896 particles in a
+    block: the state reads back exactly, and 60 substeps of it springing back
+    match the oracle with every particle accounted for."""
+    gel = I.Gel(8, 8, 8, 0.625e-3, seed=11)
+    sc = I.Scene(gel, I.Material(E=1.5e5, nu=0.3), I.no_indenter(),
+                 I.keyframes([(0, 2.5e-3, 2.5e-3, 20e-3, 0.0)]), I.Solver(dt=1e-5, relrest_limit=1),
+                 readout_every=20, readout_px=8, readout_pitch=gel.dx, n_substeps=60, name="squeezed")
+    x, v, C, F, tag = _init(sc)
+    x[:, 2] *= 0.5
+    F[:, 8] = 0.5
+    state = (x, v, C, F, tag)
+    sim = T.Sim(sc, states=[state])
+    xr, vr, Cr, Fr = sim.particles()
+    assert np.array_equal(xr, x) and np.array_equal(Fr, F)
+    st0 = sim.stats()
+    assert st0.status == 0
+    sim.step(60)
+    xg, _, _, Fg = sim.particles()
+    stats = sim.stats()
+    sim.close()
+    st, s, ind = _oracle(sc, state)
+    O.run(s, ind, sc.keyframes, 0, 60, st)
+    # particles beyond the 768 slots of their block at the start (blocks of 4 x 4 x 4 base nodes)
+    base = np.floor(x.astype(np.float64) / gel.dx - 0.5).astype(np.int64) + np.array(gel.origin)
+    _, per_block = np.unique(base // 4, axis=0, return_counts=True)
+    over = int(np.maximum(per_block - 768, 0).sum())
+    assert over > 100
+    assert stats.status == 0 and stats.spill_max >= over, (stats.status, stats.spill_max, over)
+    assert np.abs(xg - st.x).max() < POS_TOL * gel.dx
+    assert np.abs(Fg - st.F).max() < 1e-4
+    assert st.x[:, 2].max() > x[:, 2].max() + 0.5 * gel.dx          # it sprang back up
 
 
 # ------------------------------------------------------------------ full size, sampled
@@ -278,32 +359,59 @@ def _subset(st_np, lo, hi, dx):
     return m, core[m]
 
 
-def test_pad4m_full_size_sampled_one_step():
-    """4.19M-particle pad in the benchmark's launch configuration (CUDA graph):
-    after pressing, one substep of sampled sub-boxes matches the oracle run on
-    the same snapshot (a particle's update depends only on particles within 2
-    cells), and P2G conserves mass."""
+def _tip_box(sc, k, passes, half=6):
+    """Cell box around the indenter tip at substep k: the whole gel depth and
+    +-(half + margin) cells in x and y, where the margin (2 cells per pass of
+    the substep, plus one) holds every particle that the core's update can
+    depend on; returns (lo, hi, margin)."""
+    tip = O.pose(sc.keyframes, k, sc.solver.dt, sc.ind.tip_offset).tip
+    dx = sc.gel.dx
+    tc = (int(tip[0] / dx), int(tip[1] / dx))
+    m = 2 * passes + 1
+    return (tc[0] - half - m, tc[1] - half - m, -1), (tc[0] + half + m, tc[1] + half + m, sc.gel.cz), m
+
+
+def test_pad4m_full_size_sampled_press_slip_rotate():
+    """4.19M-particle pad in the benchmark's launch configuration (CUDA graph),
+    in each phase of its trajectory (press at substep 600, slip at 8000,
+    rotation at 14000): one substep of the region around the indenter, where
+    the relative-rest loop runs, matches the oracle run on the same snapshot,
+    pass count included.  The region is the tip's column of cells widened by
+    2 cells per pass (a particle's update in one pass depends only on
+    particles within 2 cells); P2G conserves mass."""
     sc = I.scene_pad4m(seed=0)
     sim = T.Sim(sc, use_graph=True)
-    sim.step(600)
-    x, v, C, F = sim.particles()
     tag = I.gel_particles(sc.gel)[1]
-    g = sim.grid()
-    mp = sc.mat.rho * sc.gel.dx ** 3 / 8
-    assert abs(g[:, 0].astype(np.float64).sum() / (x.shape[0] * mp) - 1) < 1e-4
-    sim.step(1)
-    x1, v1, C1, F1 = sim.particles()
-    gp, _ = sim.log(1)
-    sim.close()
     dx = sc.gel.dx
     s, ind = O.make_scene(sc), O.make_indenter(sc.ind)
-    assert gp[0] == 1
-    for lo, hi in [((56, 56, 26), (72, 72, 31)), ((0, 0, -1), (10, 10, 6)), ((100, 60, 20), (110, 70, 31))]:
-        m, core = _subset((x,), lo, hi, dx)
-        st = O.State(x[m], v[m], C[m], F[m], tag[m])
-        O.substep(s, ind, sc.keyframes, 600, st)
-        assert np.abs(x1[m][core] - st.x[core]).max() < 1e-4 * dx
-        assert np.abs(F1[m][core] - st.F[core]).max() < 1e-5
+    mp = sc.mat.rho * dx ** 3 / 8
+    k = 0
+    seen = []
+    for target in (600, 8000, 14000):
+        sim.step(target - k)
+        k = target
+        x, v, C, F = sim.particles()
+        if target == 600:
+            g = sim.grid()
+            assert abs(g[:, 0].astype(np.float64).sum() / (x.shape[0] * mp) - 1) < 1e-4
+        sim.step(1)
+        k += 1
+        x1, v1, C1, F1 = sim.particles()
+        gp, _ = sim.log(1)
+        lo, hi, m = _tip_box(sc, target, int(gp[0]))
+        b = np.floor(x / dx - 0.5)
+        sel = np.all((b >= np.array(lo)) & (b <= np.array(hi)), axis=1)
+        core = np.all((b[:, :2] >= np.array(lo[:2]) + m) & (b[:, :2] <= np.array(hi[:2]) - m), axis=1)[sel]
+        st = O.State(x[sel], v[sel], C[sel], F[sel], tag[sel])
+        passes, _, nc = O.substep(s, ind, sc.keyframes, target, st)
+        assert passes == gp[0], (target, passes, gp[0])
+        assert core.sum() > 10000
+        assert np.abs(x1[sel][core] - st.x[core]).max() < 1e-4 * dx, target
+        assert np.abs(F1[sel][core] - st.F[core]).max() < 1e-5, target
+        assert np.abs(v1[sel][core] - st.v[core]).max() < 1e-4 * np.abs(st.v[core]).max(), target
+        seen.append(int(gp[0]))
+    sim.close()
+    assert seen[0] == 1 and max(seen[1:]) > 1          # the loop repeats passes once the indenter slides
 
 
 # ------------------------------------------------------------------ batching
@@ -370,6 +478,30 @@ def test_large33m_prefix_sampled_one_step():
         O.substep(s, ind, sc.keyframes, 500, st)
         assert np.abs(x1[m][core] - st.x[core]).max() < 1e-4 * dx
         assert np.abs(F1[m][core] - st.F[core]).max() < 1e-5
+
+
+@pytest.mark.skipif(os.environ.get("TSIM_LONG") != "1",
+                    reason="the FP64 oracle needs about ten minutes of all host cores for this run; TSIM_LONG=1")
+def test_large33m_500_substep_prefix_matches_oracle():
+    """33,554,432-particle gel with the Perlin-bump plate: the whole
+    500-substep prefix of the trajectory on the GPU (graph mode) and on the
+    all-cores FP64 oracle from the same inputs; positions within 1e-3 dx and
+    equal pass counts."""
+    sc = I.scene_large33m()
+    state = _init(sc)
+    sim = T.Sim(sc, use_graph=True, states=[state])
+    sim.step(500)
+    x, _, _, _ = sim.particles()
+    gp, _ = sim.log(500)
+    sim.close()
+    st, s, ind = _oracle(sc, state)
+    del state
+    pl, _ = O.run_par(s, ind, sc.keyframes, 0, 500, st)
+    d = np.abs(x - st.x).max() / sc.gel.dx
+    print("large33m prefix: max |x_gpu - x_oracle| = %.3g dx over %d particles, %d oracle threads"
+          % (d, x.shape[0], O.threads()))
+    assert np.array_equal(gp, pl)
+    assert d < POS_TOL
 
 
 # ------------------------------------------------------------------ surrogate inputs and targets

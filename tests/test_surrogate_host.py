@@ -72,3 +72,16 @@ def test_serve_summary_hand_worked():
     # the network alone: 0.01 and 0.015 within 2 %
     assert s["surrogate_within"] == 0.5
     assert s["median_err"] == pytest.approx(0.0225) and s["p90_err"] == pytest.approx(0.044)
+
+
+def test_served_time_charges_the_trajectory_prefix():
+    """Hand-worked: 6 frames of two trajectories (frames at substeps 100, 200,
+    300), network 100 frames/s, IMPM 10 frames/s.  Trajectory 0 falls back at
+    its frames 1 and 2 (pays 2 IMPM frames: the run to frame 2 also gives
+    frame 1), trajectory 1 at its frame 3 (pays 3): 6/100 + 2/10 + 3/10."""
+    fb = np.array([True, True, False, False, False, True])
+    traj = np.array([0, 0, 0, 1, 1, 1])
+    sub = np.array([100, 200, 300, 100, 200, 300])
+    t = G.served_seconds(fb, traj, sub, 100, 100.0, 10.0)
+    assert t == pytest.approx(0.06 + 0.2 + 0.3)
+    assert G.served_seconds(np.zeros(6, bool), traj, sub, 100, 100.0, 10.0) == pytest.approx(0.06)
