@@ -629,9 +629,10 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
         float x[3], F[9], v[3] = {0.f, 0.f, 0.f}, C[9];
         uint32_t tag = 0;
         int cl = 255;
+        float f[3];                 // fractional offset of the staged position (reused when x stays)
+        int bx = 0, by = 0, bz = 0;
         if (valid) {
-            float f[3], w[3][3];
-            int bx, by, bz;
+            float w[3][3];
             bspline(sm.P[0][r], inv_dx, bx, f[0], w[0]);
             bspline(sm.P[1][r], inv_dx, by, f[1], w[1]);
             bspline(sm.P[2][r], inv_dx, bz, f[2], w[2]);
@@ -691,9 +692,18 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
                 err |= ST_NUMERIC;
                 valid = false;
             } else {
-                float nf[3], nw[3][3];
+                // the position that enters P2G: moved on a commit pass, else the staged one
+                float nf[3];
+                if (moves) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) bspline(x[a], inv_dx, nb[a], nf[a], nw[a]);
+                    for (int a = 0; a < 3; ++a) {
+                        float wt[3];
+                        bspline(x[a], inv_dx, nb[a], nf[a], wt);
+                    }
+                } else {
+                    nb[0] = bx; nb[1] = by; nb[2] = bz;
+                    nf[0] = f[0]; nf[1] = f[1]; nf[2] = f[2];
+                }
                 nb[0] += I.ox; nb[1] += I.oy; nb[2] += I.oz;          // box index of the new base node
                 const int wx = nb[0] - (gx0 - 1), wy = nb[1] - (gy0 - 1), wz = nb[2] - (gz0 - 1);
                 if (nb[0] < 0 || nb[1] < 0 || nb[2] < 0 || nb[0] + 2 >= I.nx || nb[1] + 2 >= I.ny ||
@@ -717,6 +727,12 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
 #pragma unroll
                         for (int c = 0; c < 3; ++c) sm.P[12 + c][r] = nf[c];
                     } else {
+                        float nw[3][3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            const float u = 1.5f - nf[a], bq = nf[a] - 1.f, cq = nf[a] - 0.5f;
+                            nw[a][0] = 0.5f * u * u; nw[a][1] = 0.75f - bq * bq; nw[a][2] = 0.5f * cq * cq;
+                        }
                         p2g_global(d.acc, I, nb[0], nb[1], nb[2], nw, nf, Q, mv, I.mp);
                         cl = 255;
                     }
