@@ -229,8 +229,8 @@ struct TransferSmem {
     float P[15][CAP];
     float4 V[GV * GV * GV];        // grid velocities of the G2P window
     unsigned short idx[CAP];       // particle order sorted by cell
-    unsigned char cell[CAP];       // cell of each particle (255: handled by global atomics / invalid)
-    int ccount[NCELL], coff[NCELL], ccur[NCELL];
+    unsigned short cell[CAP];      // cell | rank in the cell << 6 (0xffff: handled by global atomics / invalid)
+    int ccount[NCELL], coff[NCELL];
     unsigned long long bar;        // mbarrier of the bulk copies
     unsigned long long key[NT / 32];
     float tip[3];
@@ -238,14 +238,13 @@ struct TransferSmem {
 };
 
 // Per-warp node slab of the P2G combine: warp w holds the 4x4 cells of z layer
-// w, whose 3x3x3 stencils cover 6 x 6 x 3 nodes; rows padded to 8 nodes and a
-// channel stride of 146 floats (= 2 mod 16) put the two channels that the two
-// threads of a cell write in one instruction on disjoint banks.
-constexpr int SLX = 8, SLY = 6, SLZ = 3;
-constexpr int SLCH = 146;
-constexpr int SLAB = 4 * SLCH;
-static_assert(SLCH >= SLX * SLY * SLZ, "slab channel holds 6 x 6 x 3 nodes");
-static_assert((NT / 32) * SLAB <= 15 * CAP, "the slabs fit in the staging rows");
+// w, whose 3x3x3 stencils cover 6 x 6 x 3 nodes, one float4 (M, MG) per node;
+// the two threads of a cell add their channel pairs to the two halves of a
+// node's float4, and with rows of 6 nodes the 16 cells of a warp fill each
+// bank group exactly twice (two wavefronts, the minimum for 256 bytes).
+constexpr int SLX = 6, SLY = 6, SLZ = 3;
+constexpr int SLAB = SLX * SLY * SLZ;  // float4 nodes per warp slab
+static_assert((NT / 32) * SLAB * 4 <= 15 * CAP, "the slabs fit in the staging rows");
 static_assert(NT == 2 * NCELL && NCELL / (NT / 32) == 16, "two threads per cell, one z layer of cells per warp");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -258,55 +257,62 @@ __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
 // G2P of one particle from the block's velocity window (Eqs. 6-7), factorised
 // over the tensor-product weights: per (i, j) row the k-sums, per i the
-// j-sums, then the i-sum; d = x_i - x_p in cells.  Returns v and D = sum w V d^T.
+// j-sums, then the i-sum; d = x_i - x_p in cells.  Window nodes hold
+// (V_x, V_y, V_z, V_z), so one packed FMA takes both the weight and the
+// weight-times-offset sum of V_z.  Returns v and D = sum w V d^T.
 __device__ __forceinline__ void g2p_window(const float4 *__restrict__ Vw, int cx, int cy, int cz,
                                            const float w[3][3], const float f[3], float v[3], float D[9])
 {
-    float2 wx[3], wy[3], wz[3], ex[3], ey[3], ez[3];
+    float2 wx[3], wy[3], wz[3], ex[3], ey[3], ez[3], wez[3];
+    float exs[3], eys[3], wxs[3];
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
-        wx[o] = dup2(w[0][o]); ex[o] = dup2(w[0][o] * ((float)o - f[0]));
-        wy[o] = dup2(w[1][o]); ey[o] = dup2(w[1][o] * ((float)o - f[1]));
+        exs[o] = w[0][o] * ((float)o - f[0]);
+        eys[o] = w[1][o] * ((float)o - f[1]);
+        wxs[o] = w[0][o];
+        wx[o] = dup2(w[0][o]); ex[o] = dup2(exs[o]);
+        wy[o] = dup2(w[1][o]); ey[o] = dup2(eys[o]);
         wz[o] = dup2(w[2][o]); ez[o] = dup2(w[2][o] * ((float)o - f[2]));
+        wez[o] = make_float2(w[2][o], w[2][o] * ((float)o - f[2]));
     }
     const float2 z2 = make_float2(0.f, 0.f);
-    float2 vxy = z2, vz = z2, Dxxy = z2, Dxz = z2, Dyxy = z2, Dyz = z2, Dzxy = z2, Dzz = z2;
+    // v = (vxy, vzD.x), D_zz = vzD.y
+    float2 vxy = z2, vzD = z2, Dxxy = z2, Dyxy = z2, Dzxy = z2;
+    float Dxz = 0.f, Dyz = 0.f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        float2 Uxy = z2, Uz = z2, Uyxy = z2, Uyz = z2, Uzxy = z2, Uzz = z2;
+        float2 Uxy = z2, Uyxy = z2, Uzxy = z2, UzUzz = z2;
+        float Uyz = 0.f;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            float2 Txy = z2, Tz = z2, Tzxy = z2, Tzz = z2;
+            float2 Txy = z2, Tzxy = z2, Tzwe = z2;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const float4 V = Vw[((cz + k) * GV + (cy + j)) * GV + (cx + i)];
-                const float2 Vxy = make_float2(V.x, V.y), Vz = make_float2(V.z, V.w);
+                const float2 Vxy = make_float2(V.x, V.y), Vzz = make_float2(V.z, V.w);
                 Txy = ffma2(wz[k], Vxy, Txy);
-                Tz = ffma2(wz[k], Vz, Tz);
                 Tzxy = ffma2(ez[k], Vxy, Tzxy);
-                Tzz = ffma2(ez[k], Vz, Tzz);
+                Tzwe = ffma2(wez[k], Vzz, Tzwe);          // (sum wz V_z, sum ez V_z)
             }
             Uxy = ffma2(wy[j], Txy, Uxy);
-            Uz = ffma2(wy[j], Tz, Uz);
             Uyxy = ffma2(ey[j], Txy, Uyxy);
-            Uyz = ffma2(ey[j], Tz, Uyz);
             Uzxy = ffma2(wy[j], Tzxy, Uzxy);
-            Uzz = ffma2(wy[j], Tzz, Uzz);
+            UzUzz = ffma2(wy[j], Tzwe, UzUzz);           // (sum wy wz V_z, sum wy ez V_z)
+            Uyz = fmaf(eys[j], Tzwe.x, Uyz);             // sum ey wz V_z
         }
         vxy = ffma2(wx[i], Uxy, vxy);
-        vz = ffma2(wx[i], Uz, vz);
         Dxxy = ffma2(ex[i], Uxy, Dxxy);
-        Dxz = ffma2(ex[i], Uz, Dxz);
         Dyxy = ffma2(wx[i], Uyxy, Dyxy);
-        Dyz = ffma2(wx[i], Uyz, Dyz);
         Dzxy = ffma2(wx[i], Uzxy, Dzxy);
-        Dzz = ffma2(wx[i], Uzz, Dzz);
+        vzD = ffma2(wx[i], UzUzz, vzD);                  // (v_z, D_zz)
+        Dxz = fmaf(exs[i], UzUzz.x, Dxz);
+        Dyz = fmaf(wxs[i], Uyz, Dyz);
     }
-    v[0] = vxy.x; v[1] = vxy.y; v[2] = vz.x;
+    v[0] = vxy.x; v[1] = vxy.y; v[2] = vzD.x;
     // D[r][c] = sum w V_r d_c
-    D[0] = Dxxy.x; D[3] = Dxxy.y; D[6] = Dxz.x;
-    D[1] = Dyxy.x; D[4] = Dyxy.y; D[7] = Dyz.x;
-    D[2] = Dzxy.x; D[5] = Dzxy.y; D[8] = Dzz.x;
+    D[0] = Dxxy.x; D[3] = Dxxy.y; D[6] = Dxz;
+    D[1] = Dyxy.x; D[4] = Dyxy.y; D[7] = Dyz;
+    D[2] = Dzxy.x; D[5] = Dzxy.y; D[8] = vzD.y;
 }
 
 
@@ -589,7 +595,7 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
             sm.tip[0] = S->pose.tip_next[0]; sm.tip[1] = S->pose.tip_next[1]; sm.tip[2] = S->pose.tip_next[2];
         }
     }
-    if (tid < NCELL) { sm.ccount[tid] = 0; sm.ccur[tid] = 0; }
+    if (tid < NCELL) sm.ccount[tid] = 0;
     __syncthreads();
     const Inst &I = sm.inst;
     const int lb = b - I.block0;
@@ -601,6 +607,7 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
             const int ax = gx0 + lx, ay = gy0 + ly, az = gz0 + lz;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (ax < I.nx && ay < I.ny && az < I.nz) v = d.vel[node_of(I, ax, ay, az)];
+            v.w = v.z;                                   // (V_x, V_y, V_z, V_z): see g2p_window
             sm.V[t] = v;
         }
     }
@@ -615,17 +622,57 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
         return;
     }
 
-    // 1. particle-parallel pass
+    // 0b. counting sort of the staged particles by the cell of their staged
+    //     position; phase 1 then runs in cell order, so that the lanes of a
+    //     cell read the same window nodes in the G2P
     unsigned int err = 0;
+    for (int r = tid; r < count; r += NT) {
+        int bx, by, bz;
+        float ff, ww[3];
+        bspline(sm.P[0][r], inv_dx, bx, ff, ww);
+        bspline(sm.P[1][r], inv_dx, by, ff, ww);
+        bspline(sm.P[2][r], inv_dx, bz, ff, ww);
+        const int lx = bx + I.ox - gx0, ly = by + I.oy - gy0, lz = bz + I.oz - gz0;
+        unsigned short e = 0xffff;
+        if (lx < 0 || ly < 0 || lz < 0 || lx >= BLK || ly >= BLK || lz >= BLK) {
+            err |= ST_DOMAIN;
+        } else {
+            const int c = (lz * BLK + ly) * BLK + lx;
+            e = (unsigned short)(c | atomicAdd(&sm.ccount[c], 1) << 6);
+        }
+        sm.cell[r] = e;
+    }
+    __syncthreads();
+    if (tid < 32) {                                  // exclusive scan of the 64 cell counts
+        const int a0 = sm.ccount[2 * tid], a1 = sm.ccount[2 * tid + 1];
+        int incl = a0 + a1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += y;
+        }
+        const int excl = incl - a0 - a1;
+        sm.coff[2 * tid] = excl;
+        sm.coff[2 * tid + 1] = excl + a0;
+    }
+    __syncthreads();
+    for (int r = tid; r < count; r += NT) {
+        const int e = sm.cell[r];
+        if (e != 0xffff) sm.idx[sm.coff[e & 63] + (e >> 6)] = (unsigned short)r;
+    }
+    __syncthreads();
+    const int nsorted = sm.coff[NCELL - 1] + sm.ccount[NCELL - 1];
+
+    // 1. particle-parallel pass (in cell order)
     const float tip0 = sm.tip[0], tip1 = sm.tip[1], tip2 = sm.tip[2];
     float *dst = d.P[par ^ 1];
     uint32_t *dstT = d.T[par ^ 1];
     int *cntDst = d.cnt[par ^ 1];
     const bool store_vc = moves && (d.G->k_cur + 1 == d.G->k_end);
     unsigned long long best = ~0ull;
-    for (int r0 = 0; r0 < count; r0 += NT) {
-        const int r = r0 + tid;
-        bool valid = r < count;
+    for (int s0 = 0; s0 < count; s0 += NT) {
+        bool valid = s0 + tid < nsorted;
+        const int r = valid ? sm.idx[s0 + tid] : 0;
         float x[3], F[9], v[3] = {0.f, 0.f, 0.f}, C[9];
         uint32_t tag = 0;
         int cl = 255;
@@ -740,8 +787,8 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
             }
         }
         if (!valid) cl = 255;
-        if (r < count) sm.cell[r] = (unsigned char)cl;
-        if (cl != 255) atomicAdd(&sm.ccount[cl], 1);
+        // particles that left their cell (or failed) are taken out of the cell-parallel P2G
+        if (s0 + tid < nsorted && cl == 255) sm.cell[r] = 0xffff;
         if (moves) {
             // re-bin into the cell block of the new position: warp-aggregated slot claims
             unsigned int key = 0xffffffffu;
@@ -783,24 +830,6 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
     }
     if (err) atomic_or_status(S, err);
     __syncthreads();
-    if (tid < 32) {                                  // exclusive scan of the 64 cell counts
-        const int a0 = sm.ccount[2 * tid], a1 = sm.ccount[2 * tid + 1];
-        int incl = a0 + a1;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (tid >= o) incl += y;
-        }
-        const int excl = incl - a0 - a1;
-        sm.coff[2 * tid] = excl;
-        sm.coff[2 * tid + 1] = excl + a0;
-    }
-    __syncthreads();
-    for (int r = tid; r < count; r += NT) {
-        const int c = sm.cell[r];
-        if (c != 255) sm.idx[sm.coff[c] + atomicAdd(&sm.ccur[c], 1)] = (unsigned short)r;
-    }
-    __syncthreads();
 
     // 2. cell-parallel P2G: the two threads of a cell (adjacent lanes) each
     //    take two of the four channels over all the cell's particles; a
@@ -817,6 +846,7 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
         const float *rowA1 = sm.P[9 + 2 * h], *rowQ1 = sm.P[6 * h];
         for (int it = 0; it < ncl; ++it) {
             const int r = sm.idx[off + it];
+            if (sm.cell[r] == 0xffff) continue;             // left its cell: P2G done with global atomics
             const float f0 = sm.P[12][r], f1 = sm.P[13][r], f2 = sm.P[14][r];
             const float a1 = rowA1[r], q10 = rowQ1[r], q11 = rowQ1[CAP + r], q12 = rowQ1[2 * CAP + r];
             float a0 = 1.f, q00 = 0.f, q01 = 0.f, q02 = 0.f;
@@ -857,11 +887,10 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
         }
         // every warp has read its particles' rows: the rows now hold the slabs
         __syncthreads();
-        float *slab = &sm.P[0][0] + (tid >> 5) * SLAB;
-        for (int t = lane; t < SLAB; t += 32) slab[t] = 0.f;
+        float4 *slab = reinterpret_cast<float4 *>(&sm.P[0][0]) + (tid >> 5) * SLAB;
+        for (int t = lane; t < SLAB; t += 32) slab[t] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncwarp();
-        float *ch0 = slab + 2 * h * SLCH, *ch1 = ch0 + SLCH;
-        const float s0 = h ? 1.f : I.mp;              // M was accumulated per unit mass
+        float2 *half2 = reinterpret_cast<float2 *>(slab) + h;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -871,29 +900,30 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
                     // within a round the 16 cells of the warp write 16 different nodes
                     const int o = (i * 3 + j) * 3 + k;
                     const int n = (k * SLY + cly + j) * SLX + clx + i;
-                    ch0[n] += acc[o].x * s0;
-                    ch1[n] += acc[o].y;
+                    half2[2 * n] = fadd2(half2[2 * n], acc[o]);
                     __syncwarp();
                 }
     }
     __syncthreads();
     // 3. slabs -> grid: node plane z of the block window gets the slabs of the
     //    (up to three) cell layers below it; one vector atomic per touched node
-    for (int t = tid; t < (BLK + 2) * (BLK + 2) * (BLK + 2); t += NT) {
-        const int X = t % (BLK + 2), Y = (t / (BLK + 2)) % (BLK + 2), Z = t / ((BLK + 2) * (BLK + 2));
-        float m = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-        const int w0 = Z >= 2 ? Z - 2 : 0, w1 = Z < BLK ? Z : BLK - 1;
-        for (int w = w0; w <= w1; ++w) {
-            const float *sl = &sm.P[0][0] + w * SLAB + ((Z - w) * SLY + Y) * SLX + X;
-            m += sl[0];
-            g0 += sl[SLCH];
-            g1 += sl[2 * SLCH];
-            g2 += sl[3 * SLCH];
-        }
-        if (m != 0.f) {
-            const int ax = gx0 + X, ay = gy0 + Y, az = gz0 + Z;
-            if (ax < I.nx && ay < I.ny && az < I.nz)
-                atomicAdd(&d.acc[node_of(I, ax, ay, az)], make_float4(m, g0, g1, g2));
+    //    (M was accumulated per unit mass)
+    {
+        const float4 *slabs = reinterpret_cast<const float4 *>(&sm.P[0][0]);
+        const float mp = I.mp;
+        for (int t = tid; t < (BLK + 2) * (BLK + 2) * (BLK + 2); t += NT) {
+            const int X = t % (BLK + 2), Y = (t / (BLK + 2)) % (BLK + 2), Z = t / ((BLK + 2) * (BLK + 2));
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int w0 = Z >= 2 ? Z - 2 : 0, w1 = Z < BLK ? Z : BLK - 1;
+            for (int w = w0; w <= w1; ++w) {
+                const float4 q = slabs[w * SLAB + ((Z - w) * SLY + Y) * SLX + X];
+                a.x += q.x; a.y += q.y; a.z += q.z; a.w += q.w;
+            }
+            if (a.x != 0.f) {
+                const int ax = gx0 + X, ay = gy0 + Y, az = gz0 + Z;
+                if (ax < I.nx && ay < I.ny && az < I.nz)
+                    atomicAdd(&d.acc[node_of(I, ax, ay, az)], make_float4(a.x * mp, a.y, a.z, a.w));
+            }
         }
     }
     if (cands) {

@@ -1,8 +1,12 @@
-// tsurr.cu -- learned surface surrogate: convolutions as implicit GEMMs on the
-// BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate), forward, data
-// gradient and weight gradient; fused bias / skip / ReLU epilogues; nearest
-// upsampling fused into the input gather; masked loss with a residual
-// indicator channel; Adam.  Architecture and loss: include/tsurr.h.
+// tsurr.cu -- learned surface surrogate: 3x3 convolutions as implicit GEMMs
+// on the BF16 tensor cores with FP32 accumulation.  The forward
+// (k_conv_fwd_tc), the data gradient (k_conv_dgrad_tc) and the weight
+// gradient (k_conv_wgrad_tc) run on tcgen05.mma with TMEM accumulators, fed
+// by TMA tensor copies; weight gradients of output widths that are not a
+// multiple of 16 (frames below 128 x 128) keep an mma.sync m16n8k16 kernel
+// (k_conv_wgrad).  Fused bias / skip / ReLU epilogues, nearest upsampling
+// folded into the operand addressing, masked loss with a residual indicator
+// channel, Adam.  Architecture and loss: include/tsurr.h.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>   // CUtensorMap and the cuTensorMapEncodeTiled signature (entry point fetched at run time)

@@ -340,12 +340,18 @@ def time_inference(params, P: int = 128, batch: int = 256, reps: int = 20, warmu
         S.tsurr_destroy(net)
 
 
-def forward_flops(P: int = 128) -> float:
-    """Multiply-add FLOPs of one P x P frame through the nine convolutions
-    (2 per multiply-add, the 16-wide stored input and output included)."""
+def forward_flops(P: int = 128, stored: bool = False) -> float:
+    """Multiply-add FLOPs of one P x P frame through the nine convolutions (2
+    per multiply-add) on the real channels (12 inputs of the first layer, 4
+    outputs of the last); stored=True counts the 16-wide padded input and
+    output that the kernels compute."""
     tot, hw = 0.0, P * P
     sizes = [hw, hw / 4, hw / 16, hw / 64, hw / 64, hw / 16, hw / 4, hw, hw]
-    for (cin, cout), npix in zip(I.SURR_CONVS, sizes):
+    last = len(I.SURR_CONVS) - 1
+    for li, ((cin, cout), npix) in enumerate(zip(I.SURR_CONVS, sizes)):
+        if not stored:
+            cin = I.SURR_CIN if li == 0 else cin
+            cout = I.SURR_COUT if li == last else cout
         tot += 2.0 * npix * cout * 9 * cin
     return tot
 

@@ -85,3 +85,12 @@ def test_served_time_charges_the_trajectory_prefix():
     t = G.served_seconds(fb, traj, sub, 100, 100.0, 10.0)
     assert t == pytest.approx(0.06 + 0.2 + 0.3)
     assert G.served_seconds(np.zeros(6, bool), traj, sub, 100, 100.0, 10.0) == pytest.approx(0.06)
+
+
+def test_forward_flops_counts_real_channels():
+    """Hand-worked for an 8 x 8 frame: pixels per layer 64, 16, 4, 1, 1, 4,
+    16, 64, 64; real channels 12 -> 32 -> ... -> 32 -> 4; 2 x 9 FLOPs per
+    multiply-add of a 3 x 3 tap.  Sum of pixels x cin x cout = 589,824 on the
+    real channels and 622,592 with the 16-wide stored input and output."""
+    assert G.forward_flops(8) == 18 * 589824
+    assert G.forward_flops(8, stored=True) == 18 * 622592
