@@ -264,6 +264,42 @@ def surrogate_leg(n_traj=8, threshold=0.02):
             "weights": os.path.relpath(SURROGATE_WEIGHTS, ROOT), "trained": meta}
 
 
+def batch_leg(n_sub=300, warm=60, tune=600):
+    """The batched workload as an extra record: 64 uneven instances (grids
+    48x48x12 .. 128x128x32, about 105M particles) in one context, CUDA-graph
+    stepping with the autotuned launch configuration; particle-updates/s over
+    n_sub substeps after warm-up (CUDA events on the stream)."""
+    import torch
+    from paper_2405_02914_gb300 import inputs as I
+    from paper_2405_02914_gb300 import tsim as T
+    scenes = I.batch_scenes(n=64, seed=0)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    sim = T.Sim(scenes, stream=stream, use_graph=True)
+    setup_s = time.perf_counter() - t0
+    try:
+        tuning = T.tsim_autotune(sim.ctx, tune)
+        sim.step(warm)
+        s0 = sim.stats()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(n_sub)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        T.tsim_sync(sim.ctx)
+        s1 = sim.stats()
+        ms = e0.elapsed_time(e1)
+    finally:
+        sim.close()
+    n = sum(sc.gel.n_particles for sc in scenes)
+    upd = s1.particle_updates - s0.particle_updates
+    return {"value": upd / (ms * 1e-3), "unit": UNIT, "instances": len(scenes), "particles": n,
+            "substeps_timed": n_sub, "after_substeps": tune + warm,
+            "mean_passes_per_instance_substep": (s1.passes - s0.passes) / (n_sub * len(scenes)),
+            "ms": ms, "setup_s": setup_s, "tuning": tuning, "spill_max": int(s1.spill_max)}
+
+
 def workload(name, seed):
     """Scenes of a named workload and its description."""
     from paper_2405_02914_gb300 import inputs as I
@@ -343,6 +379,7 @@ def main():
     ap.add_argument("--workload", default="pad4m", choices=["pad4m", "press65k", "batch64", "large33m"])
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate vs IMPM frames/s leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched record")
     ap.add_argument("--autotune", type=int, default=600,
                     help="substeps of online launch-configuration tuning before the timed region (0: off)")
     ap.add_argument("--no-graph", action="store_true",
@@ -560,6 +597,11 @@ def main():
                                3 * args.steps * FRAMES_PER_STEP * len(scenes)) * world
     if args.workload != "pad4m":
         line["metric"] = UNIT + " (%s)" % args.workload
+    if not args.no_batch and world == 1 and args.workload == "pad4m":
+        try:
+            line["batch64"] = batch_leg()
+        except Exception as e:          # reported, never silently replaced by another path
+            line["batch64"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if not args.no_surrogate and world == 1:
         try:
             line["surrogate"] = surrogate_leg()
