@@ -89,6 +89,21 @@ int tsurr_adam(tsurr_net *net, float lr, float beta1, float beta2, float eps, in
 
 void tsurr_destroy(tsurr_net *net);
 
+/* Serving helpers (device arrays, the caller's stream, no allocation; they
+ * need no network object).  tsurr_features assembles the network input
+ * x[B,H,W,12] = [height, px, py, scalars[b][0..8]] from the indenter height
+ * maps height[B,H,W] (mm) and the per-frame scalars[B,9], with px = (x + 0.5)
+ * / W * 2 - 1 and py = (y + 0.5) / H * 2 - 1; x must be 16-byte aligned.
+ * tsurr_indicator reduces the indicator channel of y[B,H,W,4] to the
+ * predicted error per frame, out[b] = sqrt(mean over pixels of y[b,:,:,3]^2)
+ * / press[b], the quantity the fallback rule compares with its threshold.
+ * TSIM_ERR_INVALID_ARG on NULL pointers, non-positive sizes or a misaligned
+ * x. */
+int tsurr_features(const float *height, const float *scalars, int batch, int height_px, int width_px, float *x,
+                   void *stream);
+int tsurr_indicator(const float *y, const float *press, int batch, int height_px, int width_px, float *out,
+                    void *stream);
+
 #ifdef __cplusplus
 }
 #endif

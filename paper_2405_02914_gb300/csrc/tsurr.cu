@@ -1746,3 +1746,73 @@ extern "C" int tsurr_adam(tsurr_net *n, float lr, float b1, float b2, float eps,
     k_adam<<<cdiv(n->nparam, 256), 256, 0, n->s>>>(n->p, n->g, n->m1, n->m2, n->nparam, lr, b1, b2, eps, c1, c2);
     return refresh_weights(n);
 }
+
+// ---------------------------------------------------------------- serving helpers
+
+namespace {
+
+// x[b, y, x, :] = [h, px, py, s_0 .. s_8] with px = (x + 0.5) / W * 2 - 1 and
+// py = (y + 0.5) / H * 2 - 1: one thread per pixel, three 16-byte stores.
+__global__ void k_features(const float *__restrict__ h, const float *__restrict__ sc, long long npix, int H, int W,
+                           float *__restrict__ x)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npix) return;
+    const long long hw = (long long)H * W;
+    const long long b = t / hw;
+    const int rem = (int)(t - b * hw);
+    const int yy = rem / W, xx = rem - yy * W;
+    const float *s = sc + b * 9;
+    float4 *o = reinterpret_cast<float4 *>(x + t * 12);
+    o[0] = make_float4(h[t], ((float)xx + 0.5f) / (float)W * 2.f - 1.f, ((float)yy + 0.5f) / (float)H * 2.f - 1.f,
+                       s[0]);
+    o[1] = make_float4(s[1], s[2], s[3], s[4]);
+    o[2] = make_float4(s[5], s[6], s[7], s[8]);
+}
+
+// One CTA per frame: sqrt(mean over the pixels of y[..., 3]^2) / press.
+__global__ void __launch_bounds__(256) k_indicator(const float *__restrict__ y, const float *__restrict__ press,
+                                                   int HW, float *__restrict__ out)
+{
+    __shared__ float part[8];
+    const float *yb = y + (long long)blockIdx.x * HW * 4;
+    float s = 0.f;
+    for (int p = threadIdx.x; p < HW; p += blockDim.x) {
+        const float e = yb[(long long)p * 4 + 3];
+        s = fmaf(e, e, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += part[w];
+        out[blockIdx.x] = sqrtf(a / (float)HW) / press[blockIdx.x];
+    }
+}
+
+}  // namespace
+
+extern "C" int tsurr_features(const float *height, const float *scalars, int batch, int height_px, int width_px,
+                              float *x, void *stream)
+{
+    if (!height || !scalars || !x || batch < 1 || height_px < 1 || width_px < 1)
+        return sfail(TSIM_ERR_INVALID_ARG, "tsurr_features: bad arguments");
+    if ((uintptr_t)x % 16 != 0) return sfail(TSIM_ERR_INVALID_ARG, "tsurr_features: x must be 16-byte aligned");
+    const long long npix = (long long)batch * height_px * width_px;
+    k_features<<<(unsigned int)((npix + 255) / 256), 256, 0, (cudaStream_t)stream>>>(height, scalars, npix, height_px,
+                                                                                    width_px, x);
+    SCU(cudaGetLastError());
+    return TSIM_OK;
+}
+
+extern "C" int tsurr_indicator(const float *y, const float *press, int batch, int height_px, int width_px,
+                               float *out, void *stream)
+{
+    if (!y || !press || !out || batch < 1 || height_px < 1 || width_px < 1)
+        return sfail(TSIM_ERR_INVALID_ARG, "tsurr_indicator: bad arguments");
+    k_indicator<<<batch, 256, 0, (cudaStream_t)stream>>>(y, press, height_px * width_px, out);
+    SCU(cudaGetLastError());
+    return TSIM_OK;
+}

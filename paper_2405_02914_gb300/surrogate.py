@@ -183,18 +183,11 @@ def generate(scenes, every: int = 100, batch: int = 64, log=None, retries: int =
 
 
 def features(fr: Frames, idx=None):
-    """Network input x[B, P, P, 12] for frames ``idx`` (all when None)."""
-    torch = _torch()
+    """Network input x[B, P, P, 12] for frames ``idx`` (all when None),
+    assembled by the library's kernel (tsurr_features)."""
     h = fr.height if idx is None else fr.height[idx]
     sc = fr.scalars if idx is None else fr.scalars[idx]
-    B, P, _ = h.shape
-    lin = (torch.arange(P, device=h.device, dtype=torch.float32) + 0.5) / P * 2 - 1
-    x = torch.empty((B, P, P, 12), dtype=torch.float32, device=h.device)
-    x[..., 0] = h
-    x[..., 1] = lin.view(1, 1, P)
-    x[..., 2] = lin.view(1, P, 1)
-    x[..., 3:] = sc.view(B, 1, 1, N_SCALARS)
-    return x
+    return S.tsurr_features(h.contiguous(), sc.contiguous())
 
 
 def train(fr: Frames, steps: int, batch: int = 32, lr: float = 1e-3, seed: int = 0, params=None, log=None,
@@ -261,10 +254,11 @@ def frame_errors(pred, fr: Frames):
 
 
 def indicator(pred, fr: Frames):
-    """Predicted per-frame RMS error (indicator channel), divided by press depth."""
+    """Predicted per-frame RMS error (indicator channel), divided by press
+    depth, reduced by the library's kernel (tsurr_indicator)."""
     torch = _torch()
-    e = pred[..., 3]
-    return torch.sqrt((e * e).mean(dim=(1, 2))).cpu().numpy() / fr.press
+    press = torch.as_tensor(np.asarray(fr.press, np.float32), device=pred.device)
+    return S.tsurr_indicator(pred.contiguous(), press).cpu().numpy().astype(np.float64)
 
 
 def foil(fr: Frames, sigma_px: float):

@@ -17,7 +17,8 @@ TSURR_CIN = 12
 TSURR_COUT = 4
 
 EXPORTS = ["tsurr_create", "tsurr_num_params", "tsurr_set_params", "tsurr_get_params", "tsurr_get_grads",
-           "tsurr_forward", "tsurr_backward", "tsurr_adam", "tsurr_sync", "tsurr_destroy"]
+           "tsurr_forward", "tsurr_backward", "tsurr_adam", "tsurr_sync", "tsurr_destroy", "tsurr_features",
+           "tsurr_indicator"]
 
 # (cin, cout, stride, upsample, relu, skip source layer or -1) per layer; the
 # network input is padded from 12 to 16 channels, the output stored as 16.
@@ -44,6 +45,8 @@ def load():
             "tsurr_adam": (C.c_int, [vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int]),
             "tsurr_sync": (C.c_int, [vp]),
             "tsurr_destroy": (None, [vp]),
+            "tsurr_features": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, vp, vp]),
+            "tsurr_indicator": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -140,3 +143,30 @@ def tsurr_sync(net):
 def tsurr_destroy(net):
     if net:
         load().tsurr_destroy(net)
+
+
+def _dev(t):
+    """A contiguous float32 CUDA tensor (the helpers take device arrays only)."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"):
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def tsurr_features(height, scalars, out=None, stream=None):
+    """Network input x[B,H,W,12] from height maps [B,H,W] and scalars [B,9] (device tensors)."""
+    import torch
+    B, H, W = height.shape
+    if out is None:
+        out = torch.empty((B, H, W, 12), dtype=torch.float32, device=height.device)
+    _t._check(load().tsurr_features(_dev(height), _dev(scalars), B, H, W, _dev(out), _t._stream_handle(stream)))
+    return out
+
+
+def tsurr_indicator(y, press, out=None, stream=None):
+    """Predicted per-frame error sqrt(mean(y[...,3]^2)) / press (device tensors)."""
+    import torch
+    B, H, W, _ = y.shape
+    if out is None:
+        out = torch.empty((B,), dtype=torch.float32, device=y.device)
+    _t._check(load().tsurr_indicator(_dev(y), _dev(press), B, H, W, _dev(out), _t._stream_handle(stream)))
+    return out

@@ -164,3 +164,28 @@ def test_device_pointers_and_bad_batch():
             S.tsurr_forward(net, np.zeros((3, H, W, 12), np.float32))
     finally:
         S.tsurr_destroy(net)
+
+
+def test_serving_helpers_match_their_definitions():
+    """The feature assembly and the indicator reduction of the serving path
+    (tsurr_features, tsurr_indicator) against their definitions written out
+    in numpy on random inputs of a ragged size."""
+    import torch
+    rng = np.random.default_rng(3)
+    B, H, W = 5, 24, 40
+    h = rng.standard_normal((B, H, W)).astype(np.float32)
+    sc = rng.standard_normal((B, 9)).astype(np.float32)
+    x = S.tsurr_features(torch.from_numpy(h).cuda(), torch.from_numpy(sc).cuda()).cpu().numpy()
+    px = ((np.arange(W, dtype=np.float32) + np.float32(0.5)) / np.float32(W)) * np.float32(2) - np.float32(1)
+    py = ((np.arange(H, dtype=np.float32) + np.float32(0.5)) / np.float32(H)) * np.float32(2) - np.float32(1)
+    ref = np.empty((B, H, W, 12), np.float32)
+    ref[..., 0] = h
+    ref[..., 1] = px[None, None, :]
+    ref[..., 2] = py[None, :, None]
+    ref[..., 3:] = sc[:, None, None, :]
+    assert np.array_equal(x, ref)
+    y = rng.standard_normal((B, H, W, 4)).astype(np.float32)
+    press = rng.uniform(0.3, 1.0, B).astype(np.float32)
+    ind = S.tsurr_indicator(torch.from_numpy(y).cuda(), torch.from_numpy(press).cuda()).cpu().numpy()
+    want = np.sqrt((y[..., 3].astype(np.float64) ** 2).mean(axis=(1, 2))) / press
+    assert np.allclose(ind, want, rtol=1e-5)
