@@ -60,9 +60,13 @@ __global__ void k_round_begin(Dev d)
         S->e_id = -1;
     } else {
         const long long slot = (long long)(key & 0xffffffffull);
-        S->xe[0] = d.P[par][slot];
-        S->xe[1] = d.P[par][d.S + slot];
-        S->xe[2] = d.P[par][2 * d.S + slot];
+        // a cell-block slot of this instance holds block cells: position t = slot - block0 * CAP
+        const long long t = slot < I.sp0 ? slot - (long long)I.block0 * CAP : (long long)I.nblocks * CAP;
+        float xe[3];
+        slot_metres(d, I, par, t, slot, xe);
+        S->xe[0] = xe[0];
+        S->xe[1] = xe[1];
+        S->xe[2] = xe[2];
         S->e_id = (int)(d.T[par][slot] & ID_MASK);
     }
 }
@@ -137,8 +141,8 @@ __global__ void __launch_bounds__(512) k_grid_flat(Dev d)
 
 // ---------------------------------------------------------------- relative-rest check
 
-// Single CTA.  On the first pass of a substep it also advances the global
-// substep counters.  Each instance still iterating compares the tangential
+// Single CTA, one warp per instance.  On the first pass of a substep it also
+// advances the global substep counters.  Each instance still iterating compares the tangential
 // velocity at x_e with the object's (Algorithm 1) and either commits or asks
 // for another pass; a pass count >= LIMIT always commits, so the device-driven
 // loop of the graph ends after at most LIMIT passes.  Thread 0 alone sets the
@@ -152,7 +156,9 @@ __global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle
         s_first = d.ist[0].pass == 0 && d.ist[0].phase == 0;
     }
     __syncthreads();
-    for (int inst = threadIdx.x; inst < d.n_inst; inst += blockDim.x) {
+    // one warp per instance: the 27 node reads of the G2P at x_e in parallel
+    const int lane = threadIdx.x & 31;
+    for (int inst = threadIdx.x >> 5; inst < d.n_inst; inst += blockDim.x >> 5) {
         InstState *S = d.ist + inst;
         const Inst &I = d.inst[inst];
         if (S->phase != 0) continue;        // committing or done: the commit transfer follows the loop
@@ -175,30 +181,37 @@ __global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle
                     float ve0 = 0.f, ve1 = 0.f;
                     const int ax0 = base[0] + I.ox, ay0 = base[1] + I.oy, az0 = base[2] + I.oz;
                     if (ax0 >= 0 && ay0 >= 0 && az0 >= 0 && ax0 + 2 < I.nx && ay0 + 2 < I.ny && az0 + 2 < I.nz) {
-                        for (int i = 0; i < 3; ++i)
-                            for (int j = 0; j < 3; ++j)
-                                for (int k = 0; k < 3; ++k) {
-                                    const float4 V = d.vel[node_of(I, ax0 + i, ay0 + j, az0 + k)];
-                                    const float wt = w[0][i] * w[1][j] * w[2][k];
-                                    ve0 += wt * V.x;
-                                    ve1 += wt * V.y;
-                                }
+                        if (lane < 27) {
+                            const int i = lane / 9, j = (lane / 3) % 3, k = lane % 3;
+                            const float4 V = d.vel[node_of(I, ax0 + i, ay0 + j, az0 + k)];
+                            const float wt = w[0][i] * w[1][j] * w[2][k];
+                            ve0 = wt * V.x;
+                            ve1 = wt * V.y;
+                        }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            ve0 += __shfl_xor_sync(0xffffffffu, ve0, o);
+                            ve1 += __shfl_xor_sync(0xffffffffu, ve1, o);
+                        }
                     }
                     const float a = ve0 - vo[0], b = ve1 - vo[1];
                     accept = sqrtf(a * a + b * b) <= I.threshold * vot;
                 }
             }
         }
-        const int pass = S->pass + 1;
-        S->pass = pass;
-        S->passes_total += 1;
-        if (accept || pass >= I.limit) {
-            S->phase = 1;
-            const long long s = S->substeps;
-            d.log[(long long)inst * LOGN + (s % LOGN)] = make_int2(pass, S->e_id);
-            S->substeps = s + 1;
-        } else {
-            atomicOr(&s_any, 1);
+        __syncwarp();
+        if (lane == 0) {
+            const int pass = S->pass + 1;
+            S->pass = pass;
+            S->passes_total += 1;
+            if (accept || pass >= I.limit) {
+                S->phase = 1;
+                const long long s = S->substeps;
+                d.log[(long long)inst * LOGN + (s % LOGN)] = make_int2(pass, S->e_id);
+                S->substeps = s + 1;
+            } else {
+                atomicOr(&s_any, 1);
+            }
         }
     }
     __syncthreads();
@@ -219,8 +232,7 @@ __global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle
 
 enum { MODE_PROLOGUE = 0, MODE_ITER = 1, MODE_COMMIT = 2 };
 
-// Shared memory of one cell block (dynamic, ~53 KB: four CTAs fit an SM;
-// the commit variant's registers allow three, the others' four).
+// Shared memory of one cell block (dynamic, ~53 KB: four CTAs per SM).
 struct TransferSmem {
     // staged x (0..2), F (3..11) and tag bits (12) of the block's particles (TMA);
     // phase 1 overwrites a particle's entries with its P2G coefficients:
@@ -396,11 +408,13 @@ __device__ void spill_particle(const Dev &d, const Inst &I, InstState *S, int in
 #pragma unroll
     for (int c = 0; c < 9; ++c) F[c] = src[(3 + c) * SS + slot];
     const uint32_t tag = d.T[par][slot];
+    // spill slots hold metres; the stencil is found in node-box cells (box_cells)
+    const int oo[3] = {I.ox, I.oy, I.oz};
     int base[3];
     float f[3], w[3][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) bspline(x[a], I.inv_dx, base[a], f[a], w[a]);
-    const int ax0 = base[0] + I.ox, ay0 = base[1] + I.oy, az0 = base[2] + I.oz;
+    for (int a = 0; a < 3; ++a) bspline_cells(box_cells(x[a], I.inv_dx, oo[a]), base[a], f[a], w[a]);
+    const int ax0 = base[0], ay0 = base[1], az0 = base[2];
     if (ax0 < 0 || ay0 < 0 || az0 < 0 || ax0 + 2 >= I.nx || ay0 + 2 >= I.ny || az0 + 2 >= I.nz) {
         atomicOr(&S->status, ST_DOMAIN);
         return;
@@ -453,10 +467,12 @@ __device__ void spill_particle(const Dev &d, const Inst &I, InstState *S, int in
         return;
     }
     int nb[3];
-    float nf[3], nw[3][3];
+    float nf[3], nw[3][3], u[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) bspline(x[a], I.inv_dx, nb[a], nf[a], nw[a]);
-    nb[0] += I.ox; nb[1] += I.oy; nb[2] += I.oz;
+    for (int a = 0; a < 3; ++a) {
+        u[a] = box_cells(x[a], I.inv_dx, oo[a]);
+        bspline_cells(u[a], nb[a], nf[a], nw[a]);
+    }
     if (nb[0] < 0 || nb[1] < 0 || nb[2] < 0 || nb[0] + 2 >= I.nx || nb[1] + 2 >= I.ny || nb[2] + 2 >= I.nz) {
         atomicOr(&S->status, ST_DOMAIN);
         return;
@@ -476,8 +492,10 @@ __device__ void spill_particle(const Dev &d, const Inst &I, InstState *S, int in
             return;
         }
         float *dst = d.P[par ^ 1];
+        // a cell-block slot takes the position in that block's cells (exact: u minus
+        // an integer), a spill slot in metres
 #pragma unroll
-        for (int c = 0; c < 3; ++c) dst[c * SS + ds] = x[c];
+        for (int c = 0; c < 3; ++c) dst[c * SS + ds] = rr < CAP ? u[c] - (float)((nb[c] / BLK) * BLK) : x[c];
 #pragma unroll
         for (int c = 0; c < 9; ++c) dst[(3 + c) * SS + ds] = F[c];
         d.T[par ^ 1][ds] = tag;
@@ -498,7 +516,8 @@ __device__ void spill_particle(const Dev &d, const Inst &I, InstState *S, int in
         } else {
             tip[0] = S->pose.tip_next[0]; tip[1] = S->pose.tip_next[1]; tip[2] = S->pose.tip_next[2];
         }
-        const float e0 = x[0] - tip[0], e1 = x[1] - tip[1], e2 = x[2] - tip[2];
+        // candidate distances are compared in cells, as in the cell blocks
+        const float e0 = (x[0] - tip[0]) * I.inv_dx, e1 = (x[1] - tip[1]) * I.inv_dx, e2 = (x[2] - tip[2]) * I.inv_dx;
         const float dd = e0 * e0 + e1 * e1 + e2 * e2;
         const unsigned long long kk = ((unsigned long long)__float_as_uint(dd) << 32) | (unsigned int)cand;
         if (kk < *((volatile unsigned long long *)&S->e_key)) atomicMin(&S->e_key, kk);
@@ -545,7 +564,7 @@ __global__ void __launch_bounds__(NT) k_spill(Dev d)
 //   3. the slabs are summed per node and go to the grid with one vector
 //      atomic per touched node.
 template <int MODE>
-__global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
+__global__ void __launch_bounds__(NT, 4) k_transfer(Dev d, int block_offset)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TransferSmem &sm = *reinterpret_cast<TransferSmem *>(smem_raw);
@@ -627,12 +646,12 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
     //     cell read the same window nodes in the G2P
     unsigned int err = 0;
     for (int r = tid; r < count; r += NT) {
-        int bx, by, bz;
+        // staged positions are block-relative cells: the base node is the cell in the block
+        int lx, ly, lz;
         float ff, ww[3];
-        bspline(sm.P[0][r], inv_dx, bx, ff, ww);
-        bspline(sm.P[1][r], inv_dx, by, ff, ww);
-        bspline(sm.P[2][r], inv_dx, bz, ff, ww);
-        const int lx = bx + I.ox - gx0, ly = by + I.oy - gy0, lz = bz + I.oz - gz0;
+        bspline_cells(sm.P[0][r], lx, ff, ww);
+        bspline_cells(sm.P[1][r], ly, ff, ww);
+        bspline_cells(sm.P[2][r], lz, ff, ww);
         unsigned short e = 0xffff;
         if (lx < 0 || ly < 0 || lz < 0 || lx >= BLK || ly >= BLK || lz >= BLK) {
             err |= ST_DOMAIN;
@@ -664,7 +683,11 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
     const int nsorted = sm.coff[NCELL - 1] + sm.ccount[NCELL - 1];
 
     // 1. particle-parallel pass (in cell order)
-    const float tip0 = sm.tip[0], tip1 = sm.tip[1], tip2 = sm.tip[2];
+    // the next tip in this block's cells (candidate distances are compared in cells)
+    const float tip0 = box_cells(sm.tip[0], inv_dx, I.ox) - (float)gx0;
+    const float tip1 = box_cells(sm.tip[1], inv_dx, I.oy) - (float)gy0;
+    const float tip2 = box_cells(sm.tip[2], inv_dx, I.oz) - (float)gz0;
+    const float dtdx = dt * inv_dx;                 // the move in cells per unit velocity
     float *dst = d.P[par ^ 1];
     uint32_t *dstT = d.T[par ^ 1];
     int *cntDst = d.cnt[par ^ 1];
@@ -680,10 +703,10 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
         int bx = 0, by = 0, bz = 0;
         if (valid) {
             float w[3][3];
-            bspline(sm.P[0][r], inv_dx, bx, f[0], w[0]);
-            bspline(sm.P[1][r], inv_dx, by, f[1], w[1]);
-            bspline(sm.P[2][r], inv_dx, bz, f[2], w[2]);
-            const int lx = bx + I.ox - gx0, ly = by + I.oy - gy0, lz = bz + I.oz - gz0;
+            bspline_cells(sm.P[0][r], bx, f[0], w[0]);
+            bspline_cells(sm.P[1][r], by, f[1], w[1]);
+            bspline_cells(sm.P[2][r], bz, f[2], w[2]);
+            const int lx = bx, ly = by, lz = bz;
             if (lx < 0 || ly < 0 || lz < 0 || lx >= BLK || ly >= BLK || lz >= BLK) {
                 err |= ST_DOMAIN;
                 valid = false;
@@ -727,7 +750,7 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
 #pragma unroll
             for (int c = 0; c < 9; ++c) F[c] = Fn[c];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) x[c] += dt * v[c];
+            for (int c = 0; c < 3; ++c) x[c] += dtdx * v[c];
         }
         int nb[3] = {0, 0, 0};
         long long cand_slot = moves ? -1 : slot0 + r;   // commit: set where the particle is written
@@ -745,13 +768,13 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         float wt[3];
-                        bspline(x[a], inv_dx, nb[a], nf[a], wt);
+                        bspline_cells(x[a], nb[a], nf[a], wt);
                     }
                 } else {
                     nb[0] = bx; nb[1] = by; nb[2] = bz;
                     nf[0] = f[0]; nf[1] = f[1]; nf[2] = f[2];
                 }
-                nb[0] += I.ox; nb[1] += I.oy; nb[2] += I.oz;          // box index of the new base node
+                nb[0] += gx0; nb[1] += gy0; nb[2] += gz0;             // box index of the new base node
                 const int wx = nb[0] - (gx0 - 1), wy = nb[1] - (gy0 - 1), wz = nb[2] - (gz0 - 1);
                 if (nb[0] < 0 || nb[1] < 0 || nb[2] < 0 || nb[0] + 2 >= I.nx || nb[1] + 2 >= I.ny ||
                     nb[2] + 2 >= I.nz || wx < 0 || wy < 0 || wz < 0 || wx + 2 >= GA || wy + 2 >= GA ||
@@ -807,8 +830,15 @@ __global__ void __launch_bounds__(NT, 3) k_transfer(Dev d, int block_offset)
                     err |= ST_CAPACITY;
                 } else {
                     cand_slot = ds;
+                    // into the destination block's cells, or metres in a spill slot.  The
+                    // shift by -4 or 0 is exact; a shift by +4 of a q just below 0.5 can round
+                    // up to 4.5, so the result is kept below 4.5 (one ulp at most)
+                    const int g0[3] = {gx0, gy0, gz0}, oo[3] = {I.ox, I.oy, I.oz};
+                    const float q_hi = __int_as_float(0x408fffff);       // the float below 4.5
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) dst[c * SS + ds] = x[c];
+                    for (int c = 0; c < 3; ++c)
+                        dst[c * SS + ds] = rr < CAP ? fminf(x[c] - (float)((nb[c] / BLK) * BLK - g0[c]), q_hi)
+                                                    : block_to_metres(x[c], g0[c], oo[c], I.dx);
 #pragma unroll
                     for (int c = 0; c < 9; ++c) dst[(3 + c) * SS + ds] = F[c];
                     dstT[ds] = tag;
@@ -956,14 +986,14 @@ __global__ void k_bin_staged(Dev d, int inst, int par)
     const long long sid = I.id0 + t;
     float x[3] = {d.sx[sid * 3], d.sx[sid * 3 + 1], d.sx[sid * 3 + 2]};
     int ab[3];
+    float u[3];
     const int nn[3] = {I.nx, I.ny, I.nz}, oo[3] = {I.ox, I.oy, I.oz};
     bool ok = isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        int base;
         float f, w[3];
-        bspline(x[a], I.inv_dx, base, f, w);
-        ab[a] = base + oo[a];
+        u[a] = box_cells(x[a], I.inv_dx, oo[a]);
+        bspline_cells(u[a], ab[a], f, w);
         if (ab[a] < 0 || ab[a] + 2 >= nn[a]) ok = false;
     }
     const uint32_t tag = d.stag[sid];
@@ -981,8 +1011,9 @@ __global__ void k_bin_staged(Dev d, int inst, int par)
     }
     const long long SS = d.S;
     float *P = d.P[par];
+    // a cell-block slot holds the position in the block's cells, a spill slot metres
 #pragma unroll
-    for (int c = 0; c < 3; ++c) P[c * SS + slot] = x[c];
+    for (int c = 0; c < 3; ++c) P[c * SS + slot] = r < CAP ? u[c] - (float)((ab[c] / BLK) * BLK) : x[c];
 #pragma unroll
     for (int c = 0; c < 9; ++c) P[(3 + c) * SS + slot] = d.sF[sid * 9 + c];
     d.T[par][slot] = tag;
@@ -1008,8 +1039,10 @@ __global__ void k_gather(Dev d, int inst, int par)
     }
     const long long sid = I.id0 + id;
     const float *P = d.P[par];
+    float x[3];
+    slot_metres(d, I, par, t, slot, x);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) d.sx[sid * 3 + c] = P[c * SS + slot];
+    for (int c = 0; c < 3; ++c) d.sx[sid * 3 + c] = x[c];
 #pragma unroll
     for (int c = 0; c < 9; ++c) d.sF[sid * 9 + c] = P[(3 + c) * SS + slot];
 #pragma unroll
@@ -1053,10 +1086,10 @@ __global__ void k_surface_splat(Dev d, int inst, int par, float *num, float *den
     if (t >= (long long)I.nblocks * CAP + I.spc) return;
     const long long slot = inst_slot(d, I, inst, par, t);
     if (slot < 0) return;
-    const long long SS = d.S;
     if (!(d.T[par][slot] & TAG_TOP)) return;
-    const float *P = d.P[par];
-    const float x = P[slot], y = P[SS + slot], z = P[2 * SS + slot];
+    float xm[3];
+    slot_metres(d, I, par, t, slot, xm);
+    const float x = xm[0], y = xm[1], z = xm[2];
     const float px = x * inv_pitch - 0.5f, py = y * inv_pitch - 0.5f;
     const int u0 = (int)floorf(px) - 1, v0 = (int)floorf(py) - 1;
     for (int bb = v0; bb <= v0 + 3; ++bb) {
@@ -1104,14 +1137,14 @@ __global__ void k_surface_disp(Dev d, int inst, int par, const float *__restrict
     if (t >= (long long)I.nblocks * CAP + I.spc) return;
     const long long slot = inst_slot(d, I, inst, par, t);
     if (slot < 0) return;
-    const long long SS = d.S;
     const uint32_t tag = d.T[par][slot];
     if (!(tag & TAG_TOP)) return;
     const uint32_t id = tag & ID_MASK;
     if (id >= (uint32_t)I.n_particles) return;
-    const float *P = d.P[par];
+    float xm[3];
+    slot_metres(d, I, par, t, slot, xm);
     const float X = xref[(long long)id * 3], Y = xref[(long long)id * 3 + 1], Z = xref[(long long)id * 3 + 2];
-    const float ux = P[slot] - X, uy = P[SS + slot] - Y, uz = P[2 * SS + slot] - Z;
+    const float ux = xm[0] - X, uy = xm[1] - Y, uz = xm[2] - Z;
     const float px = X * inv_pitch - 0.5f, py = Y * inv_pitch - 0.5f;
     const int u0 = (int)floorf(px) - 1, v0 = (int)floorf(py) - 1;
     for (int bb = v0; bb <= v0 + 3; ++bb) {

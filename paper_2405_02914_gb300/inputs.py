@@ -288,15 +288,19 @@ def scene_pad4m(seed: int = 0, dt: float = 5e-6) -> Scene:
                  readout_px=128, readout_pitch=gel.dx, n_substeps=20000, name="pad4m")
 
 
-def scene_large33m(dt: float = 4e-6) -> Scene:
+def scene_large33m(dt: float = 4e-6, gap: float = 0.0) -> Scene:
     """Large gel: 60x60x15 mm on 256x256x64 cells (33,554,432 particles),
     Perlin-bump plate, press 1 mm / slip 3 mm / rotate 90 deg over 50,000
-    substeps, 16x16 markers every 200 substeps."""
+    substeps, 16x16 markers every 200 substeps.  ``gap`` (in cells) starts
+    the tip that far above the gel top, at the same press speed (parity
+    scenes use 0.37 so that the plate's flat face is not on a node plane)."""
     gel = Gel(256, 256, 64, 0.234375e-3, seed=5)
     H = gel.height
     ind = perlin_plate(4e-3, 4e-3, 1e-3, 0.25e-3, 0.3e-3, 4e-3, 0.5, 4, 0.5, seed=5)
-    kf = press_slip_rotate((30e-3, 30e-3, H), 1.0e-3, 3e-3, math.radians(90.0),
-                           10000, 20000, 20000)
+    g = gap * gel.dx
+    n_gap = int(round(10000 * g / 1.0e-3))
+    kf = press_slip_rotate((30e-3, 30e-3, H + g), 1.0e-3 + g, 3e-3, math.radians(90.0),
+                           10000 + n_gap, 20000, 20000)
     return Scene(gel, Material(), ind, kf, Solver(dt=dt), readout_every=200,
                  readout_px=128, readout_pitch=60e-3 / 128, n_substeps=50000,
                  name="large33m")

@@ -61,13 +61,17 @@ def _run_both(scene, nsub, graph=False, state=None):
 
 # ------------------------------------------------------------------ data movement
 
-def test_write_read_roundtrip_is_exact():
+def test_write_read_roundtrip():
+    """v, C and F come back exactly; positions are held in the cell units of
+    their cell block (x/dx + offset), so they come back to within rounding
+    of that conversion (1e-5 dx)."""
     sc = I.scene_small(cx=13, cy=9, cz=5)              # ragged: not whole cell blocks
     state = _random_state(sc)
     sim = T.Sim(sc, states=[state])
     x, v, C, F = sim.particles()
     sim.close()
-    assert np.array_equal(x, state[0]) and np.array_equal(v, state[1])
+    assert np.abs(x - state[0]).max() <= 1e-5 * sc.gel.dx
+    assert np.array_equal(v, state[1])
     assert np.array_equal(C, state[2]) and np.array_equal(F, state[3])
 
 
@@ -317,7 +321,8 @@ def test_overflowing_blocks_spill_and_match_oracle():
     to its instance's spill slots, which a companion kernel advances through
     the same pass.  An 8 x 8 x 8-cell gel squeezed into half its height
     (F = diag(1, 1, 0.5), so J = 0.5) starts with up to 896 particles in a
-    block: the state reads back exactly, and 60 substeps of it springing back
+    block: the state reads back (positions to rounding of their cell units),
+    and 60 substeps of it springing back
     match the oracle with every particle accounted for."""
     gel = I.Gel(8, 8, 8, 0.625e-3, seed=11)
     sc = I.Scene(gel, I.Material(E=1.5e5, nu=0.3), I.no_indenter(),
@@ -329,7 +334,7 @@ def test_overflowing_blocks_spill_and_match_oracle():
     state = (x, v, C, F, tag)
     sim = T.Sim(sc, states=[state])
     xr, vr, Cr, Fr = sim.particles()
-    assert np.array_equal(xr, x) and np.array_equal(Fr, F)
+    assert np.abs(xr - x).max() <= 1e-5 * gel.dx and np.array_equal(Fr, F)
     st0 = sim.stats()
     assert st0.status == 0
     sim.step(60)
@@ -486,8 +491,11 @@ def test_large33m_500_substep_prefix_matches_oracle():
     """33,554,432-particle gel with the Perlin-bump plate: the whole
     500-substep prefix of the trajectory on the GPU (graph mode) and on the
     all-cores FP64 oracle from the same inputs; positions within 1e-3 dx and
-    equal pass counts."""
-    sc = I.scene_large33m()
+    equal pass counts.  As in the other parity scenes the tip starts 0.37
+    cells above the gel (same press speed): started on the gel top, the
+    plate's flat face lies on the node plane z = H, where FP32 and FP64 may
+    take different sides of phi <= 0 for the same node."""
+    sc = I.scene_large33m(gap=0.37)
     state = _init(sc)
     sim = T.Sim(sc, use_graph=True, states=[state])
     sim.step(500)
@@ -497,9 +505,11 @@ def test_large33m_500_substep_prefix_matches_oracle():
     st, s, ind = _oracle(sc, state)
     del state
     pl, _ = O.run_par(s, ind, sc.keyframes, 0, 500, st)
-    d = np.abs(x - st.x).max() / sc.gel.dx
-    print("large33m prefix: max |x_gpu - x_oracle| = %.3g dx over %d particles, %d oracle threads"
-          % (d, x.shape[0], O.threads()))
+    dd = np.abs(x - st.x).max(axis=1) / sc.gel.dx
+    d = dd.max()
+    print("large33m prefix: max |x_gpu - x_oracle| = %.3g dx (99.99th percentile %.3g, %d above 1e-3) over %d "
+          "particles, %d oracle threads" % (d, np.percentile(dd, 99.99), int((dd > POS_TOL).sum()), x.shape[0],
+                                            O.threads()))
     assert np.array_equal(gp, pl)
     assert d < POS_TOL
 
