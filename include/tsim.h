@@ -320,6 +320,11 @@ int tsim_p2g_noalloc(const tsim_gel_desc *gel, const tsim_material *mat, float d
 /* Reason for the last failure on this thread (never NULL). */
 const char *tsim_last_error(void);
 
+/* Particle slots of one 4x4x4-cell block (the library's layout constant):
+ * particles beyond it in one block go to their instance's spill slots
+ * (TSIM_ERR_CAPACITY only when those are full too).  No GPU work. */
+int tsim_block_slots(void);
+
 /* Free the context and all its device memory (NULL is ignored). */
 void tsim_destroy(tsim_ctx *ctx);
 

@@ -81,6 +81,8 @@ static const int MARK_MAX = 4096;
 
 extern "C" const char *tsim_last_error(void) { return g_err.c_str(); }
 
+extern "C" int tsim_block_slots(void) { return block_slots(); }
+
 // used by the allocation-free entry point (tsim_noalloc.cu) to report through tsim_last_error
 void tsim_record_error(const std::string &msg) { g_err = msg; }
 
@@ -177,7 +179,7 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
         I.ind_kind = K_NONE;
         I.walls = 1;
         fill_material(I, g, m, 1e-5f);
-        I.spc = (int)std::max(4096ll, (np / 32 + 3) / 4 * 4);
+        I.spc = (int)std::max(4096ll, (np / 16 + 3) / 4 * 4);
         blocks += I.nblocks;
         long long nn = (long long)g.nx * g.ny * g.nz;
         nodes += nn;

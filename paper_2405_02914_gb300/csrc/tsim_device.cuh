@@ -18,7 +18,7 @@
 namespace tsim {
 
 constexpr int BLK = 4;               // cells per cell-block edge
-constexpr int CAP = 768;             // particle slots per cell block (1.5x the 512 of 8 ppc)
+constexpr int CAP = 640;             // particle slots per cell block (1.25x the 512 of 8 ppc; the rest spill)
 constexpr int NT = 128;              // threads of the fused transfer kernel (2 per cell)
 constexpr int GV = 6;                // G2P node window edge (BLK + 2)
 constexpr int GA = 8;                // P2G node window edge (BLK + 4: +-1 cell of motion)

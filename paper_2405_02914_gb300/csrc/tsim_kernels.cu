@@ -232,16 +232,17 @@ __global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle
 
 enum { MODE_PROLOGUE = 0, MODE_ITER = 1, MODE_COMMIT = 2 };
 
-// Shared memory of one cell block (dynamic, ~53 KB: four CTAs per SM).
+// Shared memory of one cell block (dynamic, 44 KB: five CTAs per SM).
 struct TransferSmem {
     // staged x (0..2), F (3..11) and tag bits (12) of the block's particles (TMA);
     // phase 1 overwrites a particle's entries with its P2G coefficients:
-    // Q (0..8), m v (9..11), fractional offset f of the new position (12..14);
-    // after phase 2 has read them the rows hold the per-warp node slabs
+    // Q (0..8), m v (9..11), fractional offset f of the new position (12..14;
+    // -1 in row 12: the particle left its cell).  Row 13 holds the sort keys
+    // (cell | rank in the cell << 6, -1: invalid) until phase 1 starts; after
+    // phase 2 has read the rows they hold the per-warp node slabs
     float P[15][CAP];
     float4 V[GV * GV * GV];        // grid velocities of the G2P window
     unsigned short idx[CAP];       // particle order sorted by cell
-    unsigned short cell[CAP];      // cell | rank in the cell << 6 (0xffff: handled by global atomics / invalid)
     int ccount[NCELL], coff[NCELL];
     unsigned long long bar;        // mbarrier of the bulk copies
     unsigned long long key[NT / 32];
@@ -564,7 +565,7 @@ __global__ void __launch_bounds__(NT) k_spill(Dev d)
 //   3. the slabs are summed per node and go to the grid with one vector
 //      atomic per touched node.
 template <int MODE>
-__global__ void __launch_bounds__(NT, 4) k_transfer(Dev d, int block_offset)
+__global__ void __launch_bounds__(NT, 5) k_transfer(Dev d, int block_offset)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TransferSmem &sm = *reinterpret_cast<TransferSmem *>(smem_raw);
@@ -652,14 +653,14 @@ __global__ void __launch_bounds__(NT, 4) k_transfer(Dev d, int block_offset)
         bspline_cells(sm.P[0][r], lx, ff, ww);
         bspline_cells(sm.P[1][r], ly, ff, ww);
         bspline_cells(sm.P[2][r], lz, ff, ww);
-        unsigned short e = 0xffff;
+        int e = -1;
         if (lx < 0 || ly < 0 || lz < 0 || lx >= BLK || ly >= BLK || lz >= BLK) {
             err |= ST_DOMAIN;
         } else {
             const int c = (lz * BLK + ly) * BLK + lx;
-            e = (unsigned short)(c | atomicAdd(&sm.ccount[c], 1) << 6);
+            e = c | atomicAdd(&sm.ccount[c], 1) << 6;
         }
-        sm.cell[r] = e;
+        reinterpret_cast<int *>(sm.P[13])[r] = e;
     }
     __syncthreads();
     if (tid < 32) {                                  // exclusive scan of the 64 cell counts
@@ -676,8 +677,8 @@ __global__ void __launch_bounds__(NT, 4) k_transfer(Dev d, int block_offset)
     }
     __syncthreads();
     for (int r = tid; r < count; r += NT) {
-        const int e = sm.cell[r];
-        if (e != 0xffff) sm.idx[sm.coff[e & 63] + (e >> 6)] = (unsigned short)r;
+        const int e = reinterpret_cast<const int *>(sm.P[13])[r];
+        if (e >= 0) sm.idx[sm.coff[e & 63] + (e >> 6)] = (unsigned short)r;
     }
     __syncthreads();
     const int nsorted = sm.coff[NCELL - 1] + sm.ccount[NCELL - 1];
@@ -811,7 +812,7 @@ __global__ void __launch_bounds__(NT, 4) k_transfer(Dev d, int block_offset)
         }
         if (!valid) cl = 255;
         // particles that left their cell (or failed) are taken out of the cell-parallel P2G
-        if (s0 + tid < nsorted && cl == 255) sm.cell[r] = 0xffff;
+        if (s0 + tid < nsorted && cl == 255) sm.P[12][r] = -1.f;
         if (moves) {
             // re-bin into the cell block of the new position: warp-aggregated slot claims
             unsigned int key = 0xffffffffu;
@@ -876,8 +877,9 @@ __global__ void __launch_bounds__(NT, 4) k_transfer(Dev d, int block_offset)
         const float *rowA1 = sm.P[9 + 2 * h], *rowQ1 = sm.P[6 * h];
         for (int it = 0; it < ncl; ++it) {
             const int r = sm.idx[off + it];
-            if (sm.cell[r] == 0xffff) continue;             // left its cell: P2G done with global atomics
-            const float f0 = sm.P[12][r], f1 = sm.P[13][r], f2 = sm.P[14][r];
+            const float f0 = sm.P[12][r];
+            if (f0 < 0.f) continue;                         // left its cell: P2G done with global atomics
+            const float f1 = sm.P[13][r], f2 = sm.P[14][r];
             const float a1 = rowA1[r], q10 = rowQ1[r], q11 = rowQ1[CAP + r], q12 = rowQ1[2 * CAP + r];
             float a0 = 1.f, q00 = 0.f, q01 = 0.f, q02 = 0.f;
             if (h) { a0 = sm.P[10][r]; q00 = sm.P[3][r]; q01 = sm.P[4][r]; q02 = sm.P[5][r]; }
@@ -1230,16 +1232,28 @@ void launch_check(const Dev &d, cudaGraphConditionalHandle h, int use_cond, cuda
     k_check<<<1, 256, 0, s>>>(d, h, use_cond);
 }
 
+// the transfer kernels take the largest shared-memory carveout, so that five
+// CTAs of 44 KB fit on an SM
+template <int MODE>
+static cudaError_t setup_transfer(int bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_transfer<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_transfer<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 cudaError_t setup_kernels()
 {
     const int bytes = (int)sizeof(TransferSmem);
-    cudaError_t e = cudaFuncSetAttribute(k_transfer<MODE_PROLOGUE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_transfer<MODE_ITER>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_transfer<MODE_COMMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = setup_transfer<MODE_PROLOGUE>(bytes);
+    if (e == cudaSuccess) e = setup_transfer<MODE_ITER>(bytes);
+    if (e == cudaSuccess) e = setup_transfer<MODE_COMMIT>(bytes);
     return e;
 }
+
+int block_slots() { return CAP; }
 
 void launch_transfer(const Dev &d, int mode, int block_offset, int nblocks, cudaStream_t s)
 {

@@ -25,6 +25,7 @@ void launch_surface_disp(const Dev &d, int inst, long long positions, int par, c
 void launch_indenter_height(const Dev &d, int inst, float *h, int W, int H, float pitch, float clip, cudaStream_t s);
 cudaError_t setup_kernels();
 size_t transfer_smem_bytes();
+int block_slots();
 
 void *fn_round_begin();
 void *fn_grid(int flat);

@@ -24,7 +24,7 @@ EXPORTS = ["tsim_create", "tsim_set_solver", "tsim_set_indenter", "tsim_set_traj
            "tsim_write_particles", "tsim_set_substep", "tsim_step", "tsim_read_particles",
            "tsim_read_grid", "tsim_read_surface", "tsim_read_markers", "tsim_read_log", "tsim_sync",
            "tsim_stats", "tsim_use_graph", "tsim_profile", "tsim_kernel_time", "tsim_pass_time", "tsim_last_error",
-           "tsim_destroy", "tsim_p2g_noalloc", "tsim_read_displacement", "tsim_read_indenter_height",
+           "tsim_block_slots", "tsim_destroy", "tsim_p2g_noalloc", "tsim_read_displacement", "tsim_read_indenter_height",
            "tsim_set_tuning", "tsim_get_tuning", "tsim_autotune"]
 
 
@@ -106,6 +106,7 @@ def load():
             "tsim_kernel_time": (C.c_int, [vp, P(C.c_int64), P(C.c_double)]),
             "tsim_pass_time": (C.c_int, [vp, P(C.c_int64), P(C.c_double), P(C.c_double)]),
             "tsim_last_error": (C.c_char_p, []),
+            "tsim_block_slots": (C.c_int, []),
             "tsim_destroy": (None, [vp]),
             "tsim_p2g_noalloc": (C.c_int, [P(GelDesc), P(MaterialDesc), C.c_float, vp, vp, vp, vp, C.c_int,
                                            vp, vp]),
@@ -367,6 +368,11 @@ def tsim_autotune(ctx, n) -> dict:
 def tsim_destroy(ctx):
     if ctx:
         load().tsim_destroy(ctx)
+
+
+def tsim_block_slots() -> int:
+    """Particle slots of one 4x4x4-cell block (the rest spill)."""
+    return int(load().tsim_block_slots())
 
 
 # ------------------------------------------------------------------ convenience wrapper

@@ -77,6 +77,8 @@ def test_invalid_arguments_rejected_without_gpu():
     assert L.tsim_get_tuning(None, C.byref(t)) == 1
     assert L.tsim_autotune(None, 600, None) == 1
     L.tsim_destroy(None)
+    # the block capacity: 1.25x the 512 particles of a full block at 8 per cell
+    assert tsim.tsim_block_slots() == 640
 
 
 def test_descriptors_from_inputs():

@@ -302,10 +302,11 @@ def test_errors_are_latched_not_faults():
     with pytest.raises(T.TsimError) as e:
         T.Sim(sc, states=[(bad, v, C, F, tag)])
     assert e.value.code == 5
-    # every particle in one cell block: 768 slots there and 4096 spill slots
-    # (the instance's minimum) hold 4864 of these 8192 particles
+    # every particle in one cell block: its slots (640) and 4096 spill slots
+    # (the instance's minimum) hold fewer than these 8192 particles
     big = I.scene_small(cx=16, cy=16, cz=4, kind=I.NONE)
     xb, vb, Cb, Fb, tb = _init(big)
+    assert T.tsim_block_slots() + 4096 < xb.shape[0]
     crowd = np.tile(xb[:1], (xb.shape[0], 1))
     with pytest.raises(T.TsimError) as e:
         T.Sim(big, states=[(crowd, vb, Cb, Fb, tb)])
@@ -317,7 +318,7 @@ def test_errors_are_latched_not_faults():
 
 
 def test_overflowing_blocks_spill_and_match_oracle():
-    """Cell blocks hold 768 slots; a block that receives more sends the rest
+    """Cell blocks hold 640 slots; a block that receives more sends the rest
     to its instance's spill slots, which a companion kernel advances through
     the same pass.  An 8 x 8 x 8-cell gel squeezed into half its height
     (F = diag(1, 1, 0.5), so J = 0.5) starts with up to 896 particles in a
@@ -343,10 +344,10 @@ def test_overflowing_blocks_spill_and_match_oracle():
     sim.close()
     st, s, ind = _oracle(sc, state)
     O.run(s, ind, sc.keyframes, 0, 60, st)
-    # particles beyond the 768 slots of their block at the start (blocks of 4 x 4 x 4 base nodes)
+    # particles beyond the slots of their block at the start (blocks of 4 x 4 x 4 base nodes)
     base = np.floor(x.astype(np.float64) / gel.dx - 0.5).astype(np.int64) + np.array(gel.origin)
     _, per_block = np.unique(base // 4, axis=0, return_counts=True)
-    over = int(np.maximum(per_block - 768, 0).sum())
+    over = int(np.maximum(per_block - T.tsim_block_slots(), 0).sum())
     assert over > 100
     assert stats.status == 0 and stats.spill_max >= over, (stats.status, stats.spill_max, over)
     assert np.abs(xg - st.x).max() < POS_TOL * gel.dx
