@@ -79,7 +79,8 @@ typedef struct tsim_ctx tsim_ctx;
 
 /* Elastomer block of cx x cy x cz cells of size dx with ppc (= 8) particles
  * per cell, inside a node box of nx x ny x nz nodes whose node (ox, oy, oz)
- * is the gel origin.  nx, ny, nz must be multiples of 4 (cell blocks). */
+ * is the gel origin.  nx, ny, nz must be multiples of 4 (cell blocks), and
+ * a node box holds fewer than 2^31 nodes. */
 typedef struct {
     int cx, cy, cz;
     int nx, ny, nz;

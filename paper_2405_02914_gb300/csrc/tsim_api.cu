@@ -154,14 +154,15 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
         bool ok = g.cx > 0 && g.cy > 0 && g.cz > 0 && g.ppc == 8 && g.dx > 0.f && std::isfinite(g.dx) &&
                   g.nx % BLK == 0 && g.ny % BLK == 0 && g.nz % BLK == 0 && g.ox >= 2 && g.oy >= 2 &&
                   g.oz >= 2 && g.ox + g.cx + 2 <= g.nx && g.oy + g.cy + 2 <= g.ny && g.oz + g.cz + 2 <= g.nz &&
-                  m.E > 0.f && m.nu >= 0.f && m.nu < 0.5f && m.rho > 0.f;
+                  m.E > 0.f && m.nu >= 0.f && m.nu < 0.5f && m.rho > 0.f &&
+                  (long long)g.nx * g.ny * g.nz < (1ll << 31);
         long long np = (long long)g.cx * g.cy * g.cz * g.ppc;
         if (!ok || np > (long long)ID_MASK) {
             delete c;
             return fail(TSIM_ERR_INVALID_ARG, "instance " + std::to_string(i) +
                                                   ": bad gel or material descriptor (node box must be a "
-                                                  "multiple of 4 and hold the gel with a 2-node margin; "
-                                                  "ppc must be 8; 0 <= nu < 0.5)");
+                                                  "multiple of 4, below 2^31 nodes, and hold the gel "
+                                                  "with a 2-node margin; ppc must be 8; 0 <= nu < 0.5)");
         }
         Inst &I = c->hinst[i];
         memset(&I, 0, sizeof(Inst));
@@ -216,6 +217,7 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
     d.n_gchunk = (long long)gch.size();
     d.S = blocks * CAP + spill;
     d.n_inst = n_inst;
+    d.n_blocks = (int)blocks;
     const size_t S = (size_t)d.S;
     struct A {
         void **p;
@@ -470,8 +472,7 @@ static int launch_substeps_stream(tsim_ctx *c, int n)
     const int limit = c->solver.relrest_limit;
     for (int s = 0; s < n; ++s) {
         launch_round_begin(c->d, c->stream);
-        launch_grid(c->d, c->max_nodes, c->grid_threads, c->grid_flat, c->stream);
-        launch_check(c->d, 0, 0, c->stream);
+        launch_grid(c->d, c->max_nodes, c->grid_threads, c->grid_flat, c->stream);   // with the check
         cudaEvent_t ew = nullptr, e0 = nullptr, e1 = nullptr;
         if (c->profile) {
             if (c->ev_used + 3 > c->ev_pool.size()) {
@@ -489,7 +490,6 @@ static int launch_substeps_stream(tsim_ctx *c, int n)
         for (int j = 1; j < limit; ++j) {
             launch_transfer(c->d, MODE_ITER_, 0, (int)c->total_blocks, c->stream);
             launch_grid(c->d, c->max_nodes, c->grid_threads, c->grid_flat, c->stream);
-            launch_check(c->d, 0, 0, c->stream);
         }
         if (c->profile) CU(cudaEventRecord(e0, c->stream));
         launch_transfer(c->d, MODE_COMMIT_, 0, (int)c->total_blocks, c->stream);
@@ -513,8 +513,9 @@ static int add_kernel(cudaGraph_t g, cudaGraphNode_t *node, const cudaGraphNode_
     return TSIM_OK;
 }
 
-// Graph of n substeps: R0 -> grid -> check -> WHILE{ transfer(ITER) -> grid -> check }
-// -> [event] -> transfer(COMMIT) -> [event], chained n times.
+// Graph of n substeps: R0 -> grid+check -> WHILE{ transfer(ITER) -> grid+check }
+// -> [event] -> transfer(COMMIT) -> [event], chained n times (the relative-rest
+// check runs in CTA 0 of every grid update launch).
 static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
 {
     cudaGraph_t g;
@@ -534,16 +535,14 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
         CU(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
         int use1 = 1;
         void *a_r0[] = {&d};
-        void *a_grid[] = {&d};
-        void *a_chk[] = {&d, &h, &use1};
+        void *a_spill[] = {&d};
+        void *a_grid[] = {&d, &h, &use1};
         void *a_tr[] = {&d, &zero};
-        cudaGraphNode_t n_r0, n_grid, n_chk, n_while, n_ev0 = nullptr, n_commit, n_ev1;
+        cudaGraphNode_t n_r0, n_chk, n_while, n_ev0 = nullptr, n_commit, n_ev1;
         rc = add_kernel(g, &n_r0, prev ? &prev : nullptr, prev ? 1 : 0, fn_round_begin(),
-                        dim3((c->n_inst + 127) / 128), dim3(128), a_r0);
+                        dim3(round_begin_ctas(d)), dim3(256), a_r0);
         if (rc) break;
-        rc = add_kernel(g, &n_grid, &n_r0, 1, fn_grid(c->grid_flat), grid_grid, grid_blk, a_grid);
-        if (rc) break;
-        rc = add_kernel(g, &n_chk, &n_grid, 1, fn_check(), dim3(1), dim3(256), a_chk);
+        rc = add_kernel(g, &n_chk, &n_r0, 1, fn_grid(c->grid_flat), grid_grid, grid_blk, a_grid);
         if (rc) break;
         cudaGraphNodeParams wp{};
         wp.type = cudaGraphNodeTypeConditional;
@@ -567,16 +566,14 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
         }
         CU(cudaGraphAddNode(&n_while, g, while_deps, nullptr, n_while_deps, &wp));
         cudaGraph_t body = wp.conditional.phGraph_out[0];
-        cudaGraphNode_t b_tr[2], b_grid, b_chk;
+        cudaGraphNode_t b_tr[2], b_chk;
         // the transfer of the cell blocks and of the spill slots run side by side
         rc = add_kernel(body, &b_tr[0], nullptr, 0, fn_transfer(MODE_ITER_), tr_grid, tr_blk, a_tr,
                         transfer_smem_bytes());
         if (rc) break;
-        rc = add_kernel(body, &b_tr[1], nullptr, 0, fn_spill(MODE_ITER_), sp_grid, tr_blk, a_grid);
+        rc = add_kernel(body, &b_tr[1], nullptr, 0, fn_spill(MODE_ITER_), sp_grid, tr_blk, a_spill);
         if (rc) break;
-        rc = add_kernel(body, &b_grid, b_tr, 2, fn_grid(c->grid_flat), grid_grid, grid_blk, a_grid);
-        if (rc) break;
-        rc = add_kernel(body, &b_chk, &b_grid, 1, fn_check(), dim3(1), dim3(256), a_chk);
+        rc = add_kernel(body, &b_chk, b_tr, 2, fn_grid(c->grid_flat), grid_grid, grid_blk, a_grid);
         if (rc) break;
         cudaGraphNode_t last = n_while;
         if (c->profile) {
@@ -587,7 +584,7 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
         rc = add_kernel(g, &n_commits[0], &last, 1, fn_transfer(MODE_COMMIT_), tr_grid, tr_blk, a_tr,
                         transfer_smem_bytes());
         if (rc) break;
-        rc = add_kernel(g, &n_commits[1], &last, 1, fn_spill(MODE_COMMIT_), sp_grid, tr_blk, a_grid);
+        rc = add_kernel(g, &n_commits[1], &last, 1, fn_spill(MODE_COMMIT_), sp_grid, tr_blk, a_spill);
         if (rc) break;
         if (c->profile) {
             CU(cudaGraphAddEventRecordNode(&n_ev1, g, n_commits, 2, out.ev.back()));

@@ -69,6 +69,7 @@ struct InstState {                 // mutable per instance
     unsigned long long e_key;      // nearest particle to the next tip: (squared-distance bits << 32) | slot
     float xe[3];
     int e_id;
+    int xs[3];                     // box index of the first node of x_e's 3x3x3 G2P stencil
     int phase;                     // 0 iterating, 1 accepted: the commit transfer moves x and F
     int pass;
     unsigned int status;
@@ -108,6 +109,7 @@ struct Dev {                       // device pointers (passed by value to kernel
     const int2 *gchunk;
     long long n_gchunk;
     int n_inst;
+    int n_blocks;                  // cell blocks of all instances
 };
 
 // Slot of the t-th particle position of instance I in parity par: t < nblocks *

@@ -1,10 +1,12 @@
 // tsim_kernels.cu -- sm_103a kernels of the IMPM substep.
 //
 // One substep (Algorithm 1) for all instances in lockstep:
-//   k_round_begin     pose of substep k (and the tip at k+1), reset pass state
+//   k_round_begin     pose of substep k (and the tip at k+1), reset pass state,
+//                     x_e and its stencil, empty the commit's cell-block counters
 //   k_grid            Eq. 5 + gravity + stick/slip SDF contact + walls + base,
-//                     one sweep over the node box; clears the P2G accumulator
-//   k_check           relative-rest check at the calibration particle x_e
+//                     one sweep over the node box; clears the P2G accumulator.
+//                     Its CTA 0 updates x_e's 27 stencil nodes itself and runs
+//                     the relative-rest check at the calibration particle x_e
 //   k_transfer<ITER>  fused G2P (Eqs. 6-7) -> P2G (Eqs. 1-4) of a repeated pass:
 //                     x and F stay, v and C go straight back to the grid
 //   k_transfer<COMMIT> fused G2P -> F, x move (Eqs. 8-9) -> re-bin into the
@@ -13,6 +15,8 @@
 // The velocity and affine field live on the grid between substeps; only x,
 // F and the tag persist per particle.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "tsim_device.cuh"
 #include "tsim_kernels.h"
@@ -31,14 +35,21 @@ __device__ __forceinline__ long long node_of(const Inst &I, int ax, int ay, int 
 
 // ---------------------------------------------------------------- round begin
 
-// One thread per instance: pose of substep k (and the tip at k+1), pass
-// state reset, and x_e of Algorithm 1 -- the particle nearest to the tip x_o
-// -- from the key that the previous commit (or prologue) left behind:
-// (squared-distance bits << 32) | slot of that particle in the current state.
-// Nothing in this kernel writes the global substep counters.
+// Thread inst of the grid, per instance: pose of substep k (and the tip at
+// k+1), pass state reset, and x_e of Algorithm 1 -- the particle nearest to
+// the tip x_o -- from the key that the previous commit (or prologue) left
+// behind: (squared-distance bits << 32) | slot of that particle in the
+// current state, with the first node of its G2P stencil.  All threads empty
+// the cell-block counters that this substep's commit fills.  Nothing in
+// this kernel writes the global substep counters.
 __global__ void k_round_begin(Dev d)
 {
-    const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    {
+        int *dst = d.cnt[d.G->par_next ^ 1];
+        for (int b = g; b < d.n_blocks; b += gridDim.x * blockDim.x) dst[b] = 0;
+    }
+    const int inst = g;
     if (inst >= d.n_inst) return;
     InstState *S = d.ist + inst;
     const Inst &I = d.inst[inst];
@@ -58,6 +69,7 @@ __global__ void k_round_begin(Dev d)
     S->e_key = ~0ull;                              // the commit of this substep fills it again
     if (key == ~0ull) {
         S->e_id = -1;
+        S->xs[0] = S->xs[1] = S->xs[2] = -1;
     } else {
         const long long slot = (long long)(key & 0xffffffffull);
         // a cell-block slot of this instance holds block cells: position t = slot - block0 * CAP
@@ -68,6 +80,14 @@ __global__ void k_round_begin(Dev d)
         S->xe[1] = xe[1];
         S->xe[2] = xe[2];
         S->e_id = (int)(d.T[par][slot] & ID_MASK);
+        const int o[3] = {I.ox, I.oy, I.oz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int b;
+            float f, w[3];
+            bspline(xe[a], I.inv_dx, b, f, w);
+            S->xs[a] = b + o[a];
+        }
     }
 }
 
@@ -78,21 +98,15 @@ __global__ void k_set_end(Dev d, long long n)
 
 // ---------------------------------------------------------------- grid update
 
-// Grid update of node t (x fastest) of instance inst: Eq. 5 + gravity, SDF
-// contact with Coulomb stick/slip, walls, base.
-__device__ __forceinline__ void grid_node(const Dev &d, int inst, long long t)
+// Grid velocity of node (ax, ay, az) of instance inst (box indices) from its
+// P2G sums a = (M, MG) with M > 0: Eq. 5 + gravity, SDF contact with Coulomb
+// stick/slip, walls, base.
+__device__ __forceinline__ void grid_velocity(const Dev &d, const Inst &I, const InstState *S, int inst, float4 a,
+                                              int ax, int ay, int az, float V[3])
 {
-    InstState *S = d.ist + inst;
-    if (S->phase != 0) return;
-    const Inst &I = d.inst[inst];
-    // first pass of the substep: empty the destination cell-block counters
-    if (S->pass == 0 && t < I.nblocks) d.cnt[d.G->par_next ^ 1][I.block0 + t] = 0;
-    const long long nn = (long long)I.nx * I.ny * I.nz;
-    if (t >= nn) return;
-    const float4 a = d.acc[I.node0 + t];
-    if (!(a.x > 0.f)) return;
-    const int ax = (int)(t % I.nx), ay = (int)((t / I.nx) % I.ny), az = (int)(t / ((long long)I.nx * I.ny));
-    float V[3] = {a.y / a.x + I.dt * I.g[0], a.z / a.x + I.dt * I.g[1], a.w / a.x + I.dt * I.g[2]};
+    V[0] = a.y / a.x + I.dt * I.g[0];
+    V[1] = a.z / a.x + I.dt * I.g[1];
+    V[2] = a.w / a.x + I.dt * I.g[2];
     if (I.ind_kind != K_NONE) {
         const Pose &P = S->pose;
         float xw[3] = {(ax - I.ox) * I.dx, (ay - I.oy) * I.dx, (az - I.oz) * I.dx};
@@ -119,35 +133,53 @@ __device__ __forceinline__ void grid_node(const Dev &d, int inst, long long t)
         if (I.base_mode == BASE_FIXED) V[0] = V[1] = V[2] = 0.f;
         else if (I.base_mode == BASE_SLIP) V[2] = 0.f;
     }
+}
+
+// x_e's 3x3x3 stencil (first node xs, box indices) lies inside the node box.
+__device__ __forceinline__ bool xe_stencil_inside(const Inst &I, const int xs[3])
+{
+    return xs[0] >= 0 && xs[1] >= 0 && xs[2] >= 0 && xs[0] + 2 < I.nx && xs[1] + 2 < I.ny && xs[2] + 2 < I.nz;
+}
+
+// Grid update of node t (x fastest) of instance inst by the node sweep; it
+// clears the node's P2G accumulator.  A node without mass is left as it is
+// (no G2P gives it weight).  The 27 nodes of x_e's stencil belong to the
+// check CTA of the same launch, which needs their velocities.
+__device__ __forceinline__ void grid_node(const Dev &d, int inst, long long t)
+{
+    const Inst &I = d.inst[inst];
+    const long long nn = (long long)I.nx * I.ny * I.nz;
+    if (t >= nn) return;
+    const float4 a = d.acc[I.node0 + t];
+    if (!(a.x > 0.f)) return;
+    const InstState *S = d.ist + inst;
+    // a node box has fewer than 2^31 nodes: 32-bit index arithmetic
+    const unsigned int tu = (unsigned int)t, nx = (unsigned int)I.nx, ny = (unsigned int)I.ny;
+    const unsigned int row = tu / nx;
+    const int ax = (int)(tu - row * nx), ay = (int)(row % ny), az = (int)(row / ny);
+    const int xs[3] = {S->xs[0], S->xs[1], S->xs[2]};
+    if (xe_stencil_inside(I, xs) && (unsigned)(ax - xs[0]) < 3u && (unsigned)(ay - xs[1]) < 3u &&
+        (unsigned)(az - xs[2]) < 3u)
+        return;
+    float V[3];
+    grid_velocity(d, I, S, inst, a, ax, ay, az, V);
     d.vel[I.node0 + t] = make_float4(V[0], V[1], V[2], 0.f);
     d.acc[I.node0 + t] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// one launch row per instance (blockIdx.y), sized by the largest instance
-__global__ void __launch_bounds__(512) k_grid(Dev d)
-{
-    grid_node(d, blockIdx.y, (long long)blockIdx.x * blockDim.x + threadIdx.x);
-}
-
-// one 1-D launch over all instances' node ranges packed back to back (no
-// empty CTAs for the smaller instances of an uneven batch); a CTA of up to
-// 512 threads never straddles two instances
-__global__ void __launch_bounds__(512) k_grid_flat(Dev d)
-{
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int2 e = d.gchunk[g >> 7];
-    grid_node(d, e.x, g - ((long long)e.y << 7));
-}
-
 // ---------------------------------------------------------------- relative-rest check
 
-// Single CTA, one warp per instance.  On the first pass of a substep it also
-// advances the global substep counters.  Each instance still iterating compares the tangential
-// velocity at x_e with the object's (Algorithm 1) and either commits or asks
-// for another pass; a pass count >= LIMIT always commits, so the device-driven
-// loop of the graph ends after at most LIMIT passes.  Thread 0 alone sets the
-// loop condition, once per launch.
-__global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle h, int use_cond)
+// The check CTA of a grid update launch, one warp per instance.  Its 27 lanes
+// first do the grid update of x_e's stencil nodes (the node sweep leaves them
+// out) and keep the velocities in registers; then each instance still
+// iterating compares the tangential velocity at x_e (G2P of those nodes) with
+// the object's (Algorithm 1) and either commits or asks for another pass; a
+// pass count >= LIMIT always commits, so the device-driven loop of the graph
+// ends after at most LIMIT passes.  On the first pass of a substep it also
+// advances the global substep counters.  Thread 0 alone sets the loop
+// condition, once per launch.  Nothing else in the launch reads what this
+// CTA writes.
+__device__ void check_cta(const Dev &d, cudaGraphConditionalHandle h, int use_cond)
 {
     __shared__ int s_any;
     __shared__ int s_first;
@@ -156,11 +188,24 @@ __global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle
         s_first = d.ist[0].pass == 0 && d.ist[0].phase == 0;
     }
     __syncthreads();
-    // one warp per instance: the 27 node reads of the G2P at x_e in parallel
     const int lane = threadIdx.x & 31;
+    const int si = lane / 9, sj = (lane / 3) % 3, sk = lane % 3;
     for (int inst = threadIdx.x >> 5; inst < d.n_inst; inst += blockDim.x >> 5) {
         InstState *S = d.ist + inst;
         const Inst &I = d.inst[inst];
+        const int xs[3] = {S->xs[0], S->xs[1], S->xs[2]};
+        const bool inside = xe_stencil_inside(I, xs);
+        float V[3] = {0.f, 0.f, 0.f};
+        if (inside && lane < 27) {
+            const int ax = xs[0] + si, ay = xs[1] + sj, az = xs[2] + sk;
+            const long long node = I.node0 + ((long long)az * I.ny + ay) * I.nx + ax;
+            const float4 a = d.acc[node];
+            if (a.x > 0.f) {
+                grid_velocity(d, I, S, inst, a, ax, ay, az, V);
+                d.vel[node] = make_float4(V[0], V[1], V[2], 0.f);
+                d.acc[node] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
         if (S->phase != 0) continue;        // committing or done: the commit transfer follows the loop
         bool accept = true;
         const Pose &P = S->pose;
@@ -174,25 +219,20 @@ __global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle
                 const float vot = sqrtf(vo[0] * vo[0] + vo[1] * vo[1]);
                 if (vot >= 1e-6f) {
                     // G2P (Eq. 6) of the tangential velocity at x_e
-                    int base[3];
-                    float f[3], w[3][3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) bspline(xe[a], I.inv_dx, base[a], f[a], w[a]);
                     float ve0 = 0.f, ve1 = 0.f;
-                    const int ax0 = base[0] + I.ox, ay0 = base[1] + I.oy, az0 = base[2] + I.oz;
-                    if (ax0 >= 0 && ay0 >= 0 && az0 >= 0 && ax0 + 2 < I.nx && ay0 + 2 < I.ny && az0 + 2 < I.nz) {
-                        if (lane < 27) {
-                            const int i = lane / 9, j = (lane / 3) % 3, k = lane % 3;
-                            const float4 V = d.vel[node_of(I, ax0 + i, ay0 + j, az0 + k)];
-                            const float wt = w[0][i] * w[1][j] * w[2][k];
-                            ve0 = wt * V.x;
-                            ve1 = wt * V.y;
-                        }
+                    if (inside && lane < 27) {
+                        int base[3];
+                        float f[3], w[3][3];
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            ve0 += __shfl_xor_sync(0xffffffffu, ve0, o);
-                            ve1 += __shfl_xor_sync(0xffffffffu, ve1, o);
-                        }
+                        for (int a = 0; a < 3; ++a) bspline(xe[a], I.inv_dx, base[a], f[a], w[a]);
+                        const float wt = w[0][si] * w[1][sj] * w[2][sk];
+                        ve0 = wt * V[0];
+                        ve1 = wt * V[1];
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        ve0 += __shfl_xor_sync(0xffffffffu, ve0, o);
+                        ve1 += __shfl_xor_sync(0xffffffffu, ve1, o);
                     }
                     const float a = ve0 - vo[0], b = ve1 - vo[1];
                     accept = sqrtf(a * a + b * b) <= I.threshold * vot;
@@ -226,6 +266,32 @@ __global__ void __launch_bounds__(256) k_check(Dev d, cudaGraphConditionalHandle
         }
         if (use_cond) cudaGraphSetConditional(h, s_any ? 1u : 0u);
     }
+}
+
+// The grid update with the relative-rest check: CTA 0 of the launch is the
+// check CTA, the others sweep the nodes.  One launch row per instance
+// (blockIdx.y), sized by the largest instance.
+__global__ void __launch_bounds__(512) k_grid(Dev d, cudaGraphConditionalHandle h, int use_cond)
+{
+    if (blockIdx.x == 0) {
+        if (blockIdx.y == 0) check_cta(d, h, use_cond);
+        return;
+    }
+    grid_node(d, blockIdx.y, (long long)(blockIdx.x - 1) * blockDim.x + threadIdx.x);
+}
+
+// The same as one 1-D launch over all instances' node ranges packed back to
+// back (no empty CTAs for the smaller instances of an uneven batch); a CTA of
+// up to 512 threads never straddles two instances.
+__global__ void __launch_bounds__(512) k_grid_flat(Dev d, cudaGraphConditionalHandle h, int use_cond)
+{
+    if (blockIdx.x == 0) {
+        check_cta(d, h, use_cond);
+        return;
+    }
+    const long long g = (long long)(blockIdx.x - 1) * blockDim.x + threadIdx.x;
+    const int2 e = d.gchunk[g >> 7];
+    grid_node(d, e.x, g - ((long long)e.y << 7));
 }
 
 // ---------------------------------------------------------------- fused transfer
@@ -1209,27 +1275,31 @@ __global__ void k_indenter_height(Dev d, int inst, float *h, int W, int H, float
 
 static inline unsigned int cdiv(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
 
-void launch_round_begin(const Dev &d, cudaStream_t s) { k_round_begin<<<(d.n_inst + 127) / 128, 128, 0, s>>>(d); }
+void launch_round_begin(const Dev &d, cudaStream_t s)
+{
+    k_round_begin<<<round_begin_ctas(d), 256, 0, s>>>(d);
+}
+
+// threads for one per instance and about eight counters to clear each
+unsigned int round_begin_ctas(const Dev &d)
+{
+    return (unsigned int)std::max(cdiv(d.n_inst, 256), std::min(cdiv(d.n_blocks, 256 * 8), 1024u));
+}
 void launch_set_end(const Dev &d, long long n, cudaStream_t s) { k_set_end<<<1, 1, 0, s>>>(d, n); }
 
 void grid_launch_shape(const Dev &d, long long max_nodes, int threads, int flat, dim3 &grid, dim3 &block)
 {
-    block = dim3(threads);
-    if (flat) grid = dim3((unsigned int)(d.n_gchunk * 128 / threads));
-    else grid = dim3((unsigned int)cdiv(max_nodes, threads), d.n_inst);
+    block = dim3(threads);           // CTA 0 is the check CTA
+    if (flat) grid = dim3((unsigned int)(d.n_gchunk * 128 / threads) + 1);
+    else grid = dim3((unsigned int)cdiv(max_nodes, threads) + 1, d.n_inst);
 }
 
 void launch_grid(const Dev &d, long long max_nodes, int threads, int flat, cudaStream_t s)
 {
     dim3 g, b;
     grid_launch_shape(d, max_nodes, threads, flat, g, b);
-    if (flat) k_grid_flat<<<g, b, 0, s>>>(d);
-    else k_grid<<<g, b, 0, s>>>(d);
-}
-
-void launch_check(const Dev &d, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s)
-{
-    k_check<<<1, 256, 0, s>>>(d, h, use_cond);
+    if (flat) k_grid_flat<<<g, b, 0, s>>>(d, 0, 0);
+    else k_grid<<<g, b, 0, s>>>(d, 0, 0);
 }
 
 // the transfer kernels take the largest shared-memory carveout, so that five
@@ -1312,7 +1382,6 @@ void launch_indenter_height(const Dev &d, int inst, float *h, int W, int H, floa
 // kernel handles for graph construction
 void *fn_round_begin() { return (void *)k_round_begin; }
 void *fn_grid(int flat) { return flat ? (void *)k_grid_flat : (void *)k_grid; }
-void *fn_check() { return (void *)k_check; }
 void *fn_transfer(int mode)
 {
     if (mode == MODE_PROLOGUE) return (void *)k_transfer<MODE_PROLOGUE>;

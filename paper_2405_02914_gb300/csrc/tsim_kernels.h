@@ -12,7 +12,6 @@ void launch_round_begin(const Dev &d, cudaStream_t s);
 void launch_set_end(const Dev &d, long long n, cudaStream_t s);
 void grid_launch_shape(const Dev &d, long long max_nodes, int threads, int flat, dim3 &grid, dim3 &block);
 void launch_grid(const Dev &d, long long max_nodes, int threads, int flat, cudaStream_t s);
-void launch_check(const Dev &d, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
 void launch_transfer(const Dev &d, int mode, int block_offset, int nblocks, cudaStream_t s);
 void launch_bin_staged(const Dev &d, int inst, int n, int par, cudaStream_t s);
 void launch_gather(const Dev &d, int inst, long long positions, int par, cudaStream_t s);
@@ -29,7 +28,7 @@ int block_slots();
 
 void *fn_round_begin();
 void *fn_grid(int flat);
-void *fn_check();
+unsigned int round_begin_ctas(const Dev &d);
 void *fn_transfer(int mode);
 void *fn_spill(int mode);
 

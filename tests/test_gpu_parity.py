@@ -486,33 +486,55 @@ def test_large33m_prefix_sampled_one_step():
         assert np.abs(F1[m][core] - st.F[core]).max() < 1e-5
 
 
-@pytest.mark.skipif(os.environ.get("TSIM_LONG") != "1",
-                    reason="the FP64 oracle needs about ten minutes of all host cores for this run; TSIM_LONG=1")
-def test_large33m_500_substep_prefix_matches_oracle():
-    """33,554,432-particle gel with the Perlin-bump plate: the whole
-    500-substep prefix of the trajectory on the GPU (graph mode) and on the
-    all-cores FP64 oracle from the same inputs; positions within 1e-3 dx and
-    equal pass counts.  As in the other parity scenes the tip starts 0.37
-    cells above the gel (same press speed): started on the gel top, the
-    plate's flat face lies on the node plane z = H, where FP32 and FP64 may
-    take different sides of phi <= 0 for the same node."""
-    sc = I.scene_large33m(gap=0.37)
+def _large33m_prefix(gap, n):
+    """The whole n-substep prefix of the 33,554,432-particle gel with the
+    Perlin-bump plate on the GPU (graph mode) and on the all-cores FP64
+    oracle from the same inputs: positions within 1e-3 dx, equal pass counts,
+    and the plate in contact with the gel for part of the prefix.  The tip
+    starts gap cells above the gel at the press speed (1e-7 m per substep):
+    started on the gel top, the plate's lowest point would sit exactly on
+    gel-top node (128, 128, 64) at substep 0, where FP32 and FP64 may take
+    different sides of phi <= 0."""
+    sc = I.scene_large33m(gap=gap)
     state = _init(sc)
     sim = T.Sim(sc, use_graph=True, states=[state])
-    sim.step(500)
+    sim.step(n)
     x, _, _, _ = sim.particles()
-    gp, _ = sim.log(500)
+    gp, _ = sim.log(n)
     sim.close()
     st, s, ind = _oracle(sc, state)
+    x0 = state[0].astype(np.float64)
     del state
-    pl, _ = O.run_par(s, ind, sc.keyframes, 0, 500, st)
+    pl, _ = O.run_par(s, ind, sc.keyframes, 0, n, st)
     dd = np.abs(x - st.x).max(axis=1) / sc.gel.dx
     d = dd.max()
-    print("large33m prefix: max |x_gpu - x_oracle| = %.3g dx (99.99th percentile %.3g, %d above 1e-3) over %d "
-          "particles, %d oracle threads" % (d, np.percentile(dd, 99.99), int((dd > POS_TOL).sum()), x.shape[0],
-                                            O.threads()))
+    # contact: the gel top under the plate sinks further than the gel top far
+    # from it, which only settles under gravity
+    H, dx = sc.gel.height, sc.gel.dx
+    top = x0[:, 2] > H - dx
+    r = np.hypot(x0[:, 0] - 30e-3, x0[:, 1] - 30e-3)
+    sink = (x0[:, 2] - st.x[:, 2]) / dx
+    near, far = sink[top & (r < 2e-3)].max(), sink[top & (r > 10e-3)].max()
+    print("large33m %d-substep prefix: max |x_gpu - x_oracle| = %.3g dx (99.99th percentile %.3g, %d above 1e-3) "
+          "over %d particles; gel top sank %.3g dx under the plate, %.3g dx far from it; %d oracle threads"
+          % (n, d, np.percentile(dd, 99.99), int((dd > POS_TOL).sum()), x.shape[0], near, far, O.threads()))
     assert np.array_equal(gp, pl)
     assert d < POS_TOL
+    assert near > far
+
+
+def test_large33m_100_substep_prefix_matches_oracle():
+    """Contact from substep 24 (gap 0.01 cells): about 100 s of all host
+    cores for the oracle."""
+    _large33m_prefix(0.01, 100)
+
+
+@pytest.mark.skipif(os.environ.get("TSIM_LONG") != "1",
+                    reason="the FP64 oracle needs about nine minutes of all host cores for this run; TSIM_LONG=1")
+def test_large33m_500_substep_prefix_matches_oracle():
+    """Contact from substep 118 (gap 0.05 cells), then 382 substeps of
+    pressing."""
+    _large33m_prefix(0.05, 500)
 
 
 # ------------------------------------------------------------------ surrogate inputs and targets
