@@ -591,10 +591,11 @@ def main():
         "gpu_launches": None,
         "clocks": clk,
     }
-    # own kernels launched in the timed region: per substep round_begin, grid, check,
-    # commit transfer; per repeat pass transfer, grid, check; per frame 3 readout kernels
+    # own kernels launched in the timed region: per substep round_begin, grid update
+    # (with the check), commit transfer and its spill branch; per repeat pass transfer,
+    # spill branch, grid update; per frame the step's end marker and 3 readout kernels
     line["gpu_launches"] = int(4 * substeps + 3 * max(repeat, 0) +
-                               3 * args.steps * FRAMES_PER_STEP * len(scenes)) * world
+                               (1 + 3 * len(scenes)) * args.steps * FRAMES_PER_STEP) * world
     if args.workload != "pad4m":
         line["metric"] = UNIT + " (%s)" % args.workload
     if not args.no_batch and world == 1 and args.workload == "pad4m":
