@@ -390,11 +390,17 @@ def main():
                     help="profiling aid: load a saved state and run --substeps substeps from --at, kernel by kernel")
     ap.add_argument("--at", type=int, default=0)
     ap.add_argument("--substeps", type=int, default=3)
+    ap.add_argument("--mu-kinetic", type=float, default=0.0,
+                    help="kinetic friction coefficient of the slip (0: the static one, the default workload)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     from paper_2405_02914_gb300 import inputs as I
     scenes, wl_desc = workload(args.workload, args.seed)
+    if args.mu_kinetic > 0:
+        for sc in scenes:
+            sc.ind.mu_k = min(args.mu_kinetic, sc.ind.mu)
+        wl_desc += ", kinetic friction %g" % args.mu_kinetic
     scene = scenes[0]
     if args.impl == "reference":
         return run_reference(args, scene)

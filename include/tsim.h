@@ -99,13 +99,18 @@ typedef struct {
 /* Rigid indenter.  Its pose is given by the tip (lowest point, the
  * calibration point x_o of Algorithm 1) and a yaw about the vertical axis
  * through the tip; the SDF frame centre sits tip_offset above the tip.
- * mu is the Coulomb friction coefficient of the stick/slip contact. */
+ * mu is the Coulomb friction coefficient of the stick/slip contact: a
+ * contact node sticks while |v_t| <= mu |v_n|.  mu_kinetic (<= mu; 0 or
+ * negative: mu) sets the slip, which reduces |v_t| by mu_kinetic |v_n| --
+ * a reading for the long-distance sliding that Sec. VI names as a
+ * limitation of the method. */
 typedef struct {
     int kind;
     float p[8];
     float mu;
     float tip_offset;
     int32_t perm[256];
+    float mu_kinetic;
 } tsim_indenter_desc;
 
 /* Pose keyframe: at substep `substep` the tip is at tip[] with yaw `yaw`

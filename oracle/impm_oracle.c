@@ -21,6 +21,10 @@
  *                particles get v_z = 0 after G2P (Algorithm 1)
  *   object       rigid analytic SDF; stick/slip Coulomb projection at nodes
  *                with phi <= 0 (relative rest when |v_t| <= mu |v_n|)
+ *   friction     Sec. VI names inaccurate relative sliding over long
+ *                distances as a limitation; the optional kinetic
+ *                coefficient mu_k <= mu sets the slip once |v_t| > mu |v_n|
+ *                (|v_t| is reduced by mu_k |v_n|); mu_k <= 0 means mu_k = mu
  *   check        tangential (xy) velocity of the calibration particle x_e
  *                against the object velocity there; x_o = indenter tip
  *   state        x and F are updated once, on the accepted (or last) pass
@@ -80,9 +84,10 @@ typedef struct {
     int kind;
     int pad_;
     double p[8];
-    double mu;               /* friction coefficient */
+    double mu;               /* (static) friction coefficient: stick when |v_t| <= mu |v_n| */
     double tip_offset;       /* SDF centre height above the tip */
     int perm[256];
+    double mu_k;             /* kinetic coefficient of the slip; <= 0: mu */
 } orc_indenter;
 
 typedef struct {
@@ -430,10 +435,11 @@ static long grid_update_planes(const orc_scene *s, const orc_indenter *ind, cons
                                 double vt[3] = {vr[0] - vn * nrm[0], vr[1] - vn * nrm[1], vr[2] - vn * nrm[2]};
                                 double vtl = sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
                                 double lim = ind->mu * (-vn);
+                                double muk = ind->mu_k > 0.0 ? ind->mu_k : ind->mu;
                                 if (vtl <= lim) {
                                     vr[0] = vr[1] = vr[2] = 0.0;        /* relative rest */
                                 } else {
-                                    double sc = 1.0 - lim / vtl;      /* Coulomb slip */
+                                    double sc = 1.0 - muk * (-vn) / vtl;   /* Coulomb slip */
                                     vr[0] = vt[0] * sc; vr[1] = vt[1] * sc; vr[2] = vt[2] * sc;
                                 }
                                 for (int r = 0; r < 3; ++r) Vn[r] = vr[r] + vo[r];

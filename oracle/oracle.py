@@ -49,7 +49,8 @@ class Scene(C.Structure):
 
 class Indenter(C.Structure):
     _fields_ = [("kind", C.c_int), ("pad_", C.c_int), ("p", C.c_double * 8),
-                ("mu", C.c_double), ("tip_offset", C.c_double), ("perm", C.c_int * 256)]
+                ("mu", C.c_double), ("tip_offset", C.c_double), ("perm", C.c_int * 256),
+                ("mu_k", C.c_double)]
 
 
 class Pose(C.Structure):
@@ -156,6 +157,7 @@ def make_indenter(ind) -> Indenter:
     perm = np.asarray(ind.perm, dtype=np.int32)
     for a in range(256):
         o.perm[a] = int(perm[a])
+    o.mu_k = ind.mu_k
     return o
 
 

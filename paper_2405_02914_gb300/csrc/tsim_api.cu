@@ -89,7 +89,7 @@ void tsim_record_error(const std::string &msg) { g_err = msg; }
 static void free_all(tsim_ctx *c)
 {
     Dev &d = c->d;
-    void *ptrs[] = {d.P[0], d.P[1], d.T[0], d.T[1], d.cnt[0], d.cnt[1], d.VC, d.acc, d.vel,
+    void *ptrs[] = {d.P[0], d.P[1], d.T[0], d.T[1], d.cnt[0], d.cnt[1], d.VC, d.acc, d.vel, d.sortc,
                     d.blk_inst, d.inst, d.ist, d.G, (void *)d.kf, (void *)d.perm, d.log,
                     d.sx, d.sv, d.sC, d.sF, d.stag, c->ro, c->ids, c->pick, (void *)d.gchunk};
     for (void *p : ptrs)
@@ -228,7 +228,7 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
         {(void **)&d.cnt[0], blocks * sizeof(int)},       {(void **)&d.cnt[1], blocks * sizeof(int)},
         {(void **)&d.VC, S * 12 * sizeof(float)},         {(void **)&d.acc, nodes * sizeof(float4)},
         {(void **)&d.vel, nodes * sizeof(float4)},
-        {(void **)&d.blk_inst, blocks * sizeof(int)},     {(void **)&d.inst, n_inst * sizeof(Inst)},
+        {(void **)&d.blk_inst, blocks * sizeof(int)},     {(void **)&d.sortc, blocks * SORTC * sizeof(unsigned short)},     {(void **)&d.inst, n_inst * sizeof(Inst)},
         {(void **)&d.ist, n_inst * sizeof(InstState)},    {(void **)&d.G, sizeof(Global)},
         {(void **)&d.kf, n_inst * MAX_KF * 5 * sizeof(float)},
         {(void **)&d.perm, n_inst * 256 * sizeof(int)},   {(void **)&d.log, n_inst * LOGN * sizeof(int2)},
@@ -264,6 +264,7 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
     chk(cudaMemsetAsync((void *)d.kf, 0, n_inst * MAX_KF * 5 * sizeof(float), c->stream));
     chk(cudaMemsetAsync(d.log, 0, n_inst * LOGN * sizeof(int2), c->stream));
     chk(cudaMemsetAsync(d.VC, 0, S * 12 * sizeof(float), c->stream));
+    chk(cudaMemsetAsync(d.sortc, 0, blocks * SORTC * sizeof(unsigned short), c->stream));
     chk(cudaMemcpyAsync(d.blk_inst, bi.data(), blocks * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     chk(cudaMemcpyAsync((void *)d.gchunk, gch.data(), gch.size() * sizeof(int2), cudaMemcpyHostToDevice,
                         c->stream));
@@ -335,8 +336,9 @@ extern "C" int tsim_set_indenter(tsim_ctx *c, int inst, const tsim_indenter_desc
 {
     int rc = check_ctx(c, inst);
     if (rc) return rc;
-    if (!ind || ind->kind < -1 || ind->kind > 4 || !(ind->mu >= 0.f))
-        return fail(TSIM_ERR_INVALID_ARG, "bad indenter descriptor");
+    if (!ind || ind->kind < -1 || ind->kind > 4 || !(ind->mu >= 0.f) || !std::isfinite(ind->mu_kinetic) ||
+        ind->mu_kinetic > ind->mu)
+        return fail(TSIM_ERR_INVALID_ARG, "bad indenter descriptor (mu >= 0, mu_kinetic <= mu)");
     for (int a = 0; a < 8; ++a)
         if (!std::isfinite(ind->p[a])) return fail(TSIM_ERR_INVALID_ARG, "non-finite indenter parameter");
     if (ind->kind == TSIM_PERLIN) {
@@ -350,6 +352,7 @@ extern "C" int tsim_set_indenter(tsim_ctx *c, int inst, const tsim_indenter_desc
     I.ind_kind = ind->kind;
     for (int a = 0; a < 8; ++a) I.ip[a] = ind->p[a];
     I.fric = ind->mu;
+    I.fric_k = ind->mu_kinetic > 0.f ? ind->mu_kinetic : ind->mu;
     I.tip_offset = ind->tip_offset;
     CU(cudaMemcpyAsync((void *)(c->d.perm + inst * 256), ind->perm, 256 * sizeof(int), cudaMemcpyHostToDevice,
                        c->stream));

@@ -25,6 +25,7 @@ constexpr int GA = 8;                // P2G node window edge (BLK + 4: +-1 cell 
 constexpr int GAZ = 68;              // z stride of the P2G window (64 + 4: conflict-free banks)
 constexpr int GAN = GAZ * GA;        // floats per P2G window channel
 constexpr int NCELL = BLK * BLK * BLK;
+constexpr int SORTC = CAP + 2 * NCELL;   // u16 per block of a stored cell sort: order, counts, offsets
 constexpr int MAX_KF = 64;
 constexpr int SPILL_CTAS = 16;       // extra CTAs of every transfer launch that process the spill slots
 constexpr int LOGN = 32768;           // per-substep log ring (passes, calibration particle) per instance
@@ -51,7 +52,7 @@ struct Inst {                      // per-instance constants
     float threshold;
     int ind_kind;
     float ip[8];
-    float fric, tip_offset;
+    float fric, fric_k, tip_offset;     // static (stick) and kinetic (slip) Coulomb coefficients
     int nkf;
     int spc;                       // spill slots of this instance (particles beyond a full cell block)
     long long sp0;                 // first spill slot
@@ -95,6 +96,7 @@ struct Dev {                       // device pointers (passed by value to kernel
     long long S;                   // slots per parity and component
     float4 *acc, *vel;
     int *blk_inst;
+    unsigned short *sortc;         // per cell block, the cell sort of its first repeat pass in a substep
     Inst *inst;
     InstState *ist;
     Global *G;

@@ -121,7 +121,8 @@ __device__ __forceinline__ void grid_velocity(const Dev &d, const Inst &I, const
                 float vt[3] = {vr[0] - vn * n[0], vr[1] - vn * n[1], vr[2] - vn * n[2]};
                 float vtl = sqrtf(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
                 float lim = I.fric * (-vn);
-                float sc = vtl <= lim ? 0.f : 1.f - lim / vtl;   // rest or Coulomb slip
+                // rest, or Coulomb slip with the kinetic coefficient
+                float sc = vtl <= lim ? 0.f : 1.f - I.fric_k * (-vn) / vtl;
 #pragma unroll
                 for (int r = 0; r < 3; ++r) V[r] = vt[r] * sc + vo[r];
             }
@@ -653,6 +654,10 @@ __global__ void __launch_bounds__(NT, 5) k_transfer(Dev d, int block_offset)
     const bool cands = MODE != MODE_ITER;
     const int count = min(d.cnt[par][b], CAP);          // an overflowed block was latched as an error
     if (count == 0) return;                             // no particles: no P2G, no moves, no candidate
+    // x has not moved since the first repeat pass of this substep, which
+    // stored its cell sort: the later repeat passes load it instead of sorting
+    const bool reuse = MODE == MODE_ITER && S->pass >= 2;
+    unsigned short *sortc = d.sortc + (long long)b * SORTC;
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -667,10 +672,14 @@ __global__ void __launch_bounds__(NT, 5) k_transfer(Dev d, int block_offset)
         mbar_init(&sm.bar, 1);
         if (count > 0) {
             const uint32_t bytes = (uint32_t)(((count + 3) & ~3) * 4);
-            mbar_expect_tx(&sm.bar, 13u * bytes);
+            mbar_expect_tx(&sm.bar, 13u * bytes + (reuse ? (uint32_t)(SORTC * 2) : 0u));
             const float *src = d.P[par];
             for (int c = 0; c < 12; ++c) bulk_load(sm.P[c], src + c * SS + slot0, bytes, &sm.bar);
             bulk_load(sm.P[12], d.T[par] + slot0, bytes, &sm.bar);
+            if (reuse) {
+                bulk_load(sm.idx, sortc, CAP * 2, &sm.bar);
+                bulk_load(sm.P[14], sortc + CAP, 2 * NCELL * 2, &sm.bar);   // row 14 is free until phase 1
+            }
         }
         if (MODE == MODE_PROLOGUE) {
             double t4[4], v4[4];
@@ -712,42 +721,61 @@ __global__ void __launch_bounds__(NT, 5) k_transfer(Dev d, int block_offset)
     //     position; phase 1 then runs in cell order, so that the lanes of a
     //     cell read the same window nodes in the G2P
     unsigned int err = 0;
-    for (int r = tid; r < count; r += NT) {
-        // staged positions are block-relative cells: the base node is the cell in the block
-        int lx, ly, lz;
-        float ff, ww[3];
-        bspline_cells(sm.P[0][r], lx, ff, ww);
-        bspline_cells(sm.P[1][r], ly, ff, ww);
-        bspline_cells(sm.P[2][r], lz, ff, ww);
-        int e = -1;
-        if (lx < 0 || ly < 0 || lz < 0 || lx >= BLK || ly >= BLK || lz >= BLK) {
-            err |= ST_DOMAIN;
-        } else {
-            const int c = (lz * BLK + ly) * BLK + lx;
-            e = c | atomicAdd(&sm.ccount[c], 1) << 6;
+    if (reuse) {
+        const unsigned short *st = reinterpret_cast<const unsigned short *>(sm.P[14]);
+        if (tid < NCELL) {
+            sm.ccount[tid] = st[tid];
+            sm.coff[tid] = st[NCELL + tid];
         }
-        reinterpret_cast<int *>(sm.P[13])[r] = e;
-    }
-    __syncthreads();
-    if (tid < 32) {                                  // exclusive scan of the 64 cell counts
-        const int a0 = sm.ccount[2 * tid], a1 = sm.ccount[2 * tid + 1];
-        int incl = a0 + a1;
+        __syncthreads();
+    } else {
+        for (int r = tid; r < count; r += NT) {
+            // staged positions are block-relative cells: the base node is the cell in the block
+            int lx, ly, lz;
+            float ff, ww[3];
+            bspline_cells(sm.P[0][r], lx, ff, ww);
+            bspline_cells(sm.P[1][r], ly, ff, ww);
+            bspline_cells(sm.P[2][r], lz, ff, ww);
+            int e = -1;
+            if (lx < 0 || ly < 0 || lz < 0 || lx >= BLK || ly >= BLK || lz >= BLK) {
+                err |= ST_DOMAIN;
+            } else {
+                const int c = (lz * BLK + ly) * BLK + lx;
+                e = c | atomicAdd(&sm.ccount[c], 1) << 6;
+            }
+            reinterpret_cast<int *>(sm.P[13])[r] = e;
+        }
+        __syncthreads();
+        if (tid < 32) {                                  // exclusive scan of the 64 cell counts
+            const int a0 = sm.ccount[2 * tid], a1 = sm.ccount[2 * tid + 1];
+            int incl = a0 + a1;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (tid >= o) incl += y;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (tid >= o) incl += y;
+            }
+            const int excl = incl - a0 - a1;
+            sm.coff[2 * tid] = excl;
+            sm.coff[2 * tid + 1] = excl + a0;
         }
-        const int excl = incl - a0 - a1;
-        sm.coff[2 * tid] = excl;
-        sm.coff[2 * tid + 1] = excl + a0;
+        __syncthreads();
+        for (int r = tid; r < count; r += NT) {
+            const int e = reinterpret_cast<const int *>(sm.P[13])[r];
+            if (e >= 0) sm.idx[sm.coff[e & 63] + (e >> 6)] = (unsigned short)r;
+        }
+        __syncthreads();
+        if (MODE == MODE_ITER) {
+            // the first repeat pass of the substep keeps the sort for the others
+            const int ns = sm.coff[NCELL - 1] + sm.ccount[NCELL - 1];
+            for (int i = tid; i < ns; i += NT) sortc[i] = sm.idx[i];
+            if (tid < NCELL) {
+                sortc[CAP + tid] = (unsigned short)sm.ccount[tid];
+                sortc[CAP + NCELL + tid] = (unsigned short)sm.coff[tid];
+            }
+        }
     }
-    __syncthreads();
-    for (int r = tid; r < count; r += NT) {
-        const int e = reinterpret_cast<const int *>(sm.P[13])[r];
-        if (e >= 0) sm.idx[sm.coff[e & 63] + (e >> 6)] = (unsigned short)r;
-    }
-    __syncthreads();
-    const int nsorted = sm.coff[NCELL - 1] + sm.ccount[NCELL - 1];
+    // (a stored sort holds indices below the count of the pass that made it)
+    const int nsorted = min(sm.coff[NCELL - 1] + sm.ccount[NCELL - 1], count);
 
     // 1. particle-parallel pass (in cell order)
     // the next tip in this block's cells (candidate distances are compared in cells)
@@ -1043,6 +1071,9 @@ __global__ void __launch_bounds__(NT, 5) k_transfer(Dev d, int block_offset)
 }
 
 size_t transfer_smem_bytes() { return sizeof(TransferSmem); }
+static_assert(offsetof(TransferSmem, idx) % 16 == 0 && (CAP * 2) % 16 == 0 && (2 * NCELL * 2) % 16 == 0 &&
+                  (SORTC * 2) % 16 == 0,
+              "bulk copies of the stored cell sort: 16-byte aligned, 16-byte multiples");
 
 // ---------------------------------------------------------------- staging <-> slots
 

@@ -84,7 +84,9 @@ class Material:
 
 @dataclasses.dataclass
 class Indenter:
-    """Rigid indenter: shape code, 8 shape parameters, friction, tip offset.
+    """Rigid indenter: shape code, 8 shape parameters, friction, tip offset,
+    and optionally a kinetic friction coefficient mu_k <= mu for the slip
+    (0: the slip uses mu too).
 
     params by shape (metres):
       SPHERE   [r]
@@ -99,6 +101,7 @@ class Indenter:
     mu: float
     tip_offset: float
     perm: np.ndarray = dataclasses.field(default_factory=lambda: np.arange(256, dtype=np.int32))
+    mu_k: float = 0.0
 
     def params8(self) -> np.ndarray:
         p = np.zeros(8, dtype=np.float64)

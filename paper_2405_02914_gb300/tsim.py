@@ -46,7 +46,7 @@ class MaterialDesc(C.Structure):
 
 class IndenterDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("p", C.c_float * 8), ("mu", C.c_float), ("tip_offset", C.c_float),
-                ("perm", C.c_int32 * 256)]
+                ("perm", C.c_int32 * 256), ("mu_kinetic", C.c_float)]
 
 
 class Keyframe(C.Structure):
@@ -183,6 +183,7 @@ def indenter_desc(ind) -> IndenterDesc:
     perm = np.asarray(ind.perm, dtype=np.int32)
     for a in range(256):
         o.perm[a] = int(perm[a])
+    o.mu_kinetic = ind.mu_k
     return o
 
 

@@ -466,6 +466,40 @@ def test_contact_projection_invariants():
         assert cnt == 0 and np.abs(V[node] - V_sep).max() < 1e-15
 
 
+def test_static_kinetic_friction_projection():
+    """A kinetic coefficient mu_k < mu (the long-slide reading of Sec. VI):
+    a node sticks while |v_t| <= mu |v_n|, and once it slips its tangential
+    relative speed drops by mu_k |v_n|.  Hand-worked with v_n = -0.05 m/s,
+    mu = 0.5, mu_k = 0.3: |v_t| = 0.02 sticks (it would slip under mu_k
+    alone), |v_t| = 0.04 leaves 0.04 - 0.015 = 0.025 along v_t, and with mu_k
+    unset the same node keeps 0.04 - 0.025 = 0.015."""
+    dx = 1e-3
+    gel = I.Gel(8, 8, 4, dx)
+    nx, ny, nz = gel.nodes
+    ox, oy, oz = gel.origin
+    node = ((oz + 3) * ny + oy + 4) * nx + ox + 4
+    xw = np.array([4 * dx, 4 * dx, 3 * dx])
+    kf = I.keyframes([(0, 4e-3, 4e-3, 2.5e-3, 0.0), (100, 5e-3, 4e-3, 2.5e-3, 0.5)])
+    for mu_k, t_len, want in ((0.3, 0.02, 0.0), (0.3, 0.04, 0.025), (0.0, 0.04, 0.015)):
+        ind = I.sphere(2e-3, 0.5)
+        ind.mu_k = mu_k
+        sc = I.Scene(gel, I.Material(gravity=(0.0, 0.0, 0.0)), ind, kf, I.Solver(dt=1e-5))
+        o = O.make_indenter(ind)
+        ps = O.pose(kf, 10, 1e-5, ind.tip_offset)
+        phi, n = O.sdf(o, ps, xw)
+        assert phi < 0
+        vo = np.array([ps.vlin[0] - ps.omega * (xw[1] - ps.c[1]),
+                       ps.vlin[1] + ps.omega * (xw[0] - ps.c[0]), ps.vlin[2]])
+        t_hat = np.cross(n, [1.0, 0.0, 0.0])
+        t_hat /= np.linalg.norm(t_hat)
+        s, M, MG = _one_node(sc, vo - 0.05 * n + t_len * t_hat, node)
+        V, cnt = O.grid_update(s, o, ps, M, MG)
+        assert cnt == 1
+        vr = V[node] - vo
+        assert abs(vr @ n) < 1e-15
+        assert np.abs(vr - want * t_hat).max() < 1e-15
+
+
 def test_pose_interpolation():
     kf = I.keyframes([(0, 0.01, 0.01, 0.005, 0.0), (100, 0.01, 0.01, 0.004, 0.0),
                       (300, 0.013, 0.01, 0.004, 0.0), (500, 0.013, 0.01, 0.004, 0.6)])
@@ -640,12 +674,13 @@ def test_frictionless_sphere_rotation_invariance():
     assert a.x[:, 2].min() < sc.gel.height - 0.3 * sc.gel.dx    # it did press
 
 
-def _drag_run(mu, slip=0.0, rotate=0.0, n_move=0):
+def _drag_run(mu, slip=0.0, rotate=0.0, n_move=0, mu_k=0.0):
     """Press 0.4 mm in 60 substeps, then slip along +x or turn about the
     vertical axis in n_move substeps; returns the top-layer particles within
     the contact patch at the end of the press (before, after) and the tip."""
     sc = I.scene_small(cx=12, cy=12, cz=4, n_press=60, slip=slip, n_slip=n_move if slip else 0, rotate=rotate,
                        n_rot=n_move if rotate else 0, mu=mu, press=0.4e-3)
+    sc.ind.mu_k = mu_k
     s = O.make_scene(sc)
     ind = O.make_indenter(sc.ind)
     st = _state(sc)
@@ -676,6 +711,21 @@ def test_sticking_slip_drags_the_contact_patch():
         assert abs(d[:, 1].mean()) < 0.02 * slip          # nothing across the slip direction
     assert 0.2 < out[1.0] < 1.0, out
     assert abs(out[0.0]) < 0.1, out
+
+
+def test_kinetic_friction_lowers_the_drag_of_a_long_slide():
+    """A long slide (1.5 mm, several contact radii) at mu = 1: once the
+    contact slips, a lower kinetic coefficient drags the patch less, in
+    order of mu_k (measured 0.19, 0.094, 0.020 of the slide for mu_k = 1,
+    0.6, 0.3), and never backwards.  A kinetic coefficient that is ignored,
+    or that also decides the stick, fails this."""
+    slip = 1.5e-3
+    drag = []
+    for mu_k in (0.0, 0.6, 0.3):
+        x1, x2, tip, r, top, dx = _drag_run(1.0, slip=slip, n_move=150, mu_k=mu_k)
+        patch = top & (r < 1.5 * dx)
+        drag.append((x2 - x1)[patch][:, 0].mean() / slip)
+    assert drag[0] > 1.5 * drag[1] > 0 and drag[1] > 2 * drag[2] > 0, drag
 
 
 @pytest.mark.parametrize("rotate", [0.3, -0.3])
