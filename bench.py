@@ -390,6 +390,8 @@ def main():
                     help="profiling aid: load a saved state and run --substeps substeps from --at, kernel by kernel")
     ap.add_argument("--at", type=int, default=0)
     ap.add_argument("--substeps", type=int, default=3)
+    ap.add_argument("--object-particles", action="store_true",
+                    help="represent the indenter by particles (8 per cell) instead of its SDF contact")
     ap.add_argument("--mu-kinetic", type=float, default=0.0,
                     help="kinetic friction coefficient of the slip (0: the static one, the default workload)")
     args = ap.parse_args()
@@ -397,6 +399,10 @@ def main():
 
     from paper_2405_02914_gb300 import inputs as I
     scenes, wl_desc = workload(args.workload, args.seed)
+    if args.object_particles:
+        from paper_2405_02914_gb300 import inputs as I
+        scenes = [I.with_object_particles(sc) for sc in scenes]
+        wl_desc += ", indenter as %d particles" % len(scenes[0].ind.obj)
     if args.mu_kinetic > 0:
         for sc in scenes:
             sc.ind.mu_k = min(args.mu_kinetic, sc.ind.mu)
@@ -437,6 +443,8 @@ def main():
     T.tsim_set_solver(ctx, T.solver_desc(scene.solver))
     for i, sc in enumerate(scenes):
         T.tsim_set_indenter(ctx, i, T.indenter_desc(sc.ind))
+        if sc.ind.obj is not None:
+            T.tsim_set_object_particles(ctx, i, sc.ind.obj, sc.ind.obj_m)
         T.tsim_set_trajectory(ctx, i, sc.keyframes)
     T.tsim_use_graph(ctx, not args.no_graph)
     T.tsim_profile(ctx, True)
@@ -600,7 +608,9 @@ def main():
     # own kernels launched in the timed region: per substep round_begin, grid update
     # (with the check), commit transfer and its spill branch; per repeat pass transfer,
     # spill branch, grid update; per frame the step's end marker and 3 readout kernels
-    line["gpu_launches"] = int(4 * substeps + 3 * max(repeat, 0) +
+    # (and the object particles' P2G with each transfer when the indenter is particles)
+    obj = 1 if any(sc.ind.obj is not None for sc in scenes) else 0
+    line["gpu_launches"] = int((4 + obj) * substeps + (3 + obj) * max(repeat, 0) +
                                (1 + 3 * len(scenes)) * args.steps * FRAMES_PER_STEP) * world
     if args.workload != "pad4m":
         line["metric"] = UNIT + " (%s)" % args.workload

@@ -159,6 +159,21 @@ int tsim_set_solver(tsim_ctx *ctx, const tsim_solver_desc *solver);
 /* Indenter of instance inst (host descriptor). */
 int tsim_set_indenter(tsim_ctx *ctx, int inst, const tsim_indenter_desc *ind);
 
+/* Represent the indenter of instance inst by n rigid particles (the paper's
+ * own coupling, Sec. III-A and Sec. IV-B: object particles with a
+ * prescribed velocity that take part in particle-to-grid): q holds n rows
+ * of (x, y, z) in the indenter frame (metres, about the SDF frame centre,
+ * before the yaw), each particle of the given mass.  In every pass each
+ * object particle adds to the grid at its pose position with the rigid
+ * velocity v_lin + omega z x (x - c) and that motion's affine field (Eqs.
+ * 1-3, no stress); the SDF contact projection of the grid update is then
+ * off for this instance, while the SDF still decides whether x_e is in
+ * contact for the relative-rest check.  n = 0 returns to the SDF contact.
+ * q: host or device (on_device), copied before the call returns.  n is
+ * limited to max(65536, particles / 4) per instance (reserved at create):
+ * TSIM_ERR_INVALID_ARG beyond that. */
+int tsim_set_object_particles(tsim_ctx *ctx, int inst, const float *q, int n, float mass, int on_device);
+
 /* Pose keyframes of instance inst: n_kf (1..64) rows, increasing substep.
  * Fig. 2 (B): the object moves step by step to its target pose. */
 int tsim_set_trajectory(tsim_ctx *ctx, int inst, const tsim_keyframe *kf, int n_kf,

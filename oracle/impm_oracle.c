@@ -21,6 +21,13 @@
  *                particles get v_z = 0 after G2P (Algorithm 1)
  *   object       rigid analytic SDF; stick/slip Coulomb projection at nodes
  *                with phi <= 0 (relative rest when |v_t| <= mu |v_n|)
+ *   object particles (optional, the paper's own coupling, Sec. III-A and
+ *                Sec. IV-B): the indenter as rigid particles at the pose of
+ *                the substep, each with the prescribed velocity
+ *                v_lin + omega z x (x - c), the affine field of that motion
+ *                (C = omega [[0,-1,0],[1,0,0],[0,0,0]]) and no stress, added
+ *                to the grid after the elastomer in every pass (Eqs. 1-3);
+ *                the SDF contact projection is then off
  *   friction     Sec. VI names inaccurate relative sliding over long
  *                distances as a limitation; the optional kinetic
  *                coefficient mu_k <= mu sets the slip once |v_t| > mu |v_n|
@@ -49,7 +56,10 @@
  * speed, xy components only, the out-of-contact and no-tangential-motion
  * accepts); a sticking slip or turn drags the contact
  * patch the indenter's way by less than the indenter moved, and without
- * friction it stays in place.
+ * friction it stays in place; the static/kinetic projection on hand-worked
+ * cases and a long slide whose drag falls with the kinetic coefficient;
+ * object particles transfer the rigid motion to every node exactly (with
+ * their total mass and momentum) and press the gel like the SDF contact.
  * Partly unpinned: the exact lag of the gel behind a sticking indenter over
  * long stick/slip trajectories has no closed form (checked against the
  * CUDA path).
@@ -88,6 +98,9 @@ typedef struct {
     double tip_offset;       /* SDF centre height above the tip */
     int perm[256];
     double mu_k;             /* kinetic coefficient of the slip; <= 0: mu */
+    const double *obj_q;     /* n_obj object particles in the indenter frame (x, y, z about c) */
+    long n_obj;              /* > 0: the object is these particles (no SDF contact) */
+    double obj_m;            /* mass of one object particle */
 } orc_indenter;
 
 typedef struct {
@@ -397,6 +410,40 @@ static int p2g_range(const orc_scene *s, int p0, int p1, const double *x, const 
     return ORC_OK;
 }
 
+/* Particle-to-grid of the object particles (Eqs. 1-3, no stress term), added
+ * to M and MG over the whole node box: each at the pose's world position
+ * c + R(yaw) q with the rigid velocity and affine field of the pose. */
+int orc_object_p2g(const orc_scene *s, const orc_indenter *ind, const orc_pose *ps, double *M, double *MG)
+{
+    double dx = s->dx, m = ind->obj_m;
+    double Cq[9] = {0.0, -ps->omega, 0.0, ps->omega, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long q = 0; q < ind->n_obj; ++q) {
+        const double *ql = ind->obj_q + q * 3;
+        double xw[3] = {ps->c[0] + ps->cs * ql[0] - ps->sn * ql[1], ps->c[1] + ps->sn * ql[0] + ps->cs * ql[1],
+                        ps->c[2] + ql[2]};
+        double vo[3], w[3][3];
+        int base[3];
+        object_velocity(ps, xw, vo);
+        for (int a = 0; a < 3; ++a) orc_weights(xw[a], dx, &base[a], w[a]);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    int ax = base[0] + i + s->ox, ay = base[1] + j + s->oy, az = base[2] + k + s->oz;
+                    if (ax < 0 || ay < 0 || az < 0 || ax >= s->nx || ay >= s->ny || az >= s->nz)
+                        continue;                              /* outside the node box: no grid there */
+                    long ni = node_index(s, ax, ay, az);
+                    double wip = w[0][i] * w[1][j] * w[2][k];
+                    double d[3] = {(base[0] + i) * dx - xw[0], (base[1] + j) * dx - xw[1], (base[2] + k) * dx - xw[2]};
+                    M[ni] += wip * m;                                      /* Eq. 1 */
+                    for (int r = 0; r < 3; ++r) {
+                        double Cd = Cq[r * 3 + 0] * d[0] + Cq[r * 3 + 1] * d[1] + Cq[r * 3 + 2] * d[2];
+                        MG[ni * 3 + r] += wip * m * (vo[r] + Cd);              /* Eqs. 2-3 */
+                    }
+                }
+    }
+    return ORC_OK;
+}
+
 /* Particle-to-grid of all particles in index order (the grid is cleared first). */
 int orc_p2g(const orc_scene *s, int n, const double *x, const double *v,
             const double *C, const double *F, double *M, double *MG)
@@ -423,7 +470,7 @@ static long grid_update_planes(const orc_scene *s, const orc_indenter *ind, cons
                 double Vn[3] = {0.0, 0.0, 0.0};
                 if (M[ni] > 0.0) {
                     for (int r = 0; r < 3; ++r) Vn[r] = MG[ni * 3 + r] / M[ni] + s->dt * s->g[r];
-                    if (ind->kind != ORC_NONE) {
+                    if (ind->kind != ORC_NONE && ind->n_obj <= 0) {
                         double xw[3] = {(ax - s->ox) * s->dx, (ay - s->oy) * s->dx, (az - s->oz) * s->dx};
                         double nrm[3], vo[3];
                         double phi = orc_sdf(ind, ps, xw, nrm);
@@ -554,6 +601,7 @@ int orc_substep(const orc_scene *s, const orc_indenter *ind, const double *kf, i
     for (;;) {
         rc = orc_p2g(s, n, x, v, C, F, M, MG);
         if (rc) return rc;
+        if (ind->n_obj > 0) orc_object_p2g(s, ind, &ps, M, MG);
         rc = orc_grid_update(s, ind, &ps, M, MG, V, n_contact);
         if (rc) return rc;
         rc = orc_g2p(s, n, x, tag, V, v, C);
@@ -736,11 +784,26 @@ int orc_run_par(const orc_scene *s, const orc_indenter *ind, const double *kf, i
             for (int t = 0; t < T; ++t)
                 if (ch[t].rc != ORC_OK && rc == ORC_OK) rc = ch[t].rc;
             if (rc) break;
+            if (ind->n_obj > 0) {
+                /* the object particles are added after the elastomer's sums */
 #pragma omp parallel for schedule(static, 1) num_threads(T)
-            for (int t = 0; t < T; ++t) {
-                int z0 = (int)((long)s->nz * t / T), z1 = (int)((long)s->nz * (t + 1) / T);
-                reduce_planes(s, ch, T, M, MG, z0, z1);
-                grid_update_planes(s, ind, &ps, M, MG, V, z0, z1);
+                for (int t = 0; t < T; ++t) {
+                    int z0 = (int)((long)s->nz * t / T), z1 = (int)((long)s->nz * (t + 1) / T);
+                    reduce_planes(s, ch, T, M, MG, z0, z1);
+                }
+                orc_object_p2g(s, ind, &ps, M, MG);
+#pragma omp parallel for schedule(static, 1) num_threads(T)
+                for (int t = 0; t < T; ++t) {
+                    int z0 = (int)((long)s->nz * t / T), z1 = (int)((long)s->nz * (t + 1) / T);
+                    grid_update_planes(s, ind, &ps, M, MG, V, z0, z1);
+                }
+            } else {
+#pragma omp parallel for schedule(static, 1) num_threads(T)
+                for (int t = 0; t < T; ++t) {
+                    int z0 = (int)((long)s->nz * t / T), z1 = (int)((long)s->nz * (t + 1) / T);
+                    reduce_planes(s, ch, T, M, MG, z0, z1);
+                    grid_update_planes(s, ind, &ps, M, MG, V, z0, z1);
+                }
             }
 #pragma omp parallel for schedule(static, 1) num_threads(T)
             for (int t = 0; t < T; ++t)

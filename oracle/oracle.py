@@ -50,7 +50,8 @@ class Scene(C.Structure):
 class Indenter(C.Structure):
     _fields_ = [("kind", C.c_int), ("pad_", C.c_int), ("p", C.c_double * 8),
                 ("mu", C.c_double), ("tip_offset", C.c_double), ("perm", C.c_int * 256),
-                ("mu_k", C.c_double)]
+                ("mu_k", C.c_double), ("obj_q", C.POINTER(C.c_double)), ("n_obj", C.c_long),
+                ("obj_m", C.c_double)]
 
 
 class Pose(C.Structure):
@@ -81,6 +82,8 @@ def lib():
             L.orc_p2g.argtypes = [P(Scene), C.c_int, _D, _D, _D, _D, _D, _D]
             L.orc_p2g.restype = C.c_int
             L.orc_grid_update.argtypes = [P(Scene), P(Indenter), P(Pose), _D, _D, _D, P(C.c_long)]
+            L.orc_object_p2g.argtypes = [P(Scene), P(Indenter), P(Pose), _D, _D]
+            L.orc_object_p2g.restype = C.c_int
             L.orc_grid_update.restype = C.c_int
             L.orc_g2p.argtypes = [P(Scene), C.c_int, _D, _U, _D, _D, _D]
             L.orc_g2p.restype = C.c_int
@@ -158,6 +161,12 @@ def make_indenter(ind) -> Indenter:
     for a in range(256):
         o.perm[a] = int(perm[a])
     o.mu_k = ind.mu_k
+    if getattr(ind, "obj", None) is not None and len(ind.obj):
+        q = np.ascontiguousarray(ind.obj, dtype=np.float64).reshape(-1)
+        o._obj_keep = q                       # the C struct points into this array
+        o.obj_q = q.ctypes.data_as(C.POINTER(C.c_double))
+        o.n_obj = q.size // 3
+        o.obj_m = ind.obj_m
     return o
 
 
@@ -222,6 +231,15 @@ def p2g(s: Scene, st: State):
     M = np.zeros(nn)
     MG = np.zeros(3 * nn)
     _check(lib().orc_p2g(C.byref(s), st.n, st.x, st.v, st.C, st.F, M, MG))
+    return M, MG.reshape(-1, 3)
+
+
+def object_p2g(s: Scene, ind: Indenter, ps: Pose, M=None, MG=None):
+    """The object particles' P2G added to (copies of) M, MG (zeros if None)."""
+    nn = n_nodes(s)
+    M = np.zeros(nn) if M is None else np.array(M, dtype=np.float64)
+    MG = np.zeros(3 * nn) if MG is None else np.array(MG, dtype=np.float64).reshape(-1)
+    _check(lib().orc_object_p2g(C.byref(s), C.byref(ind), C.byref(ps), M, MG))
     return M, MG.reshape(-1, 3)
 
 

@@ -53,6 +53,8 @@ struct tsim_ctx {
     std::vector<int> have_particles;
     std::vector<int> need_prologue;
     long long total_blocks = 0, total_nodes = 0, total_particles = 0, max_nodes = 0;
+    long long total_objcap = 0;
+    int max_nobj = 0;                   // most object particles of one instance (0: SDF contact everywhere)
     long long k_next = 0;
     int par_next = 0;
     // readout scratch
@@ -89,7 +91,7 @@ void tsim_record_error(const std::string &msg) { g_err = msg; }
 static void free_all(tsim_ctx *c)
 {
     Dev &d = c->d;
-    void *ptrs[] = {d.P[0], d.P[1], d.T[0], d.T[1], d.cnt[0], d.cnt[1], d.VC, d.acc, d.vel, d.sortc,
+    void *ptrs[] = {d.P[0], d.P[1], d.T[0], d.T[1], d.cnt[0], d.cnt[1], d.VC, d.acc, d.vel, d.sortc, d.objq,
                     d.blk_inst, d.inst, d.ist, d.G, (void *)d.kf, (void *)d.perm, d.log,
                     d.sx, d.sv, d.sC, d.sF, d.stag, c->ro, c->ids, c->pick, (void *)d.gchunk};
     for (void *p : ptrs)
@@ -181,6 +183,9 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
         I.walls = 1;
         fill_material(I, g, m, 1e-5f);
         I.spc = (int)std::max(4096ll, (np / 16 + 3) / 4 * 4);
+        I.objcap = (int)std::max(65536ll, np / 4);
+        I.obj0 = c->total_objcap;
+        c->total_objcap += I.objcap;
         blocks += I.nblocks;
         long long nn = (long long)g.nx * g.ny * g.nz;
         nodes += nn;
@@ -228,7 +233,8 @@ extern "C" int tsim_create(int n_inst, const tsim_gel_desc *gels, const tsim_mat
         {(void **)&d.cnt[0], blocks * sizeof(int)},       {(void **)&d.cnt[1], blocks * sizeof(int)},
         {(void **)&d.VC, S * 12 * sizeof(float)},         {(void **)&d.acc, nodes * sizeof(float4)},
         {(void **)&d.vel, nodes * sizeof(float4)},
-        {(void **)&d.blk_inst, blocks * sizeof(int)},     {(void **)&d.sortc, blocks * SORTC * sizeof(unsigned short)},     {(void **)&d.inst, n_inst * sizeof(Inst)},
+        {(void **)&d.blk_inst, blocks * sizeof(int)},     {(void **)&d.sortc, blocks * SORTC * sizeof(unsigned short)},
+        {(void **)&d.objq, (size_t)c->total_objcap * sizeof(float4)},     {(void **)&d.inst, n_inst * sizeof(Inst)},
         {(void **)&d.ist, n_inst * sizeof(InstState)},    {(void **)&d.G, sizeof(Global)},
         {(void **)&d.kf, n_inst * MAX_KF * 5 * sizeof(float)},
         {(void **)&d.perm, n_inst * 256 * sizeof(int)},   {(void **)&d.log, n_inst * LOGN * sizeof(int2)},
@@ -360,6 +366,32 @@ extern "C" int tsim_set_indenter(tsim_ctx *c, int inst, const tsim_indenter_desc
     return upload_inst(c);
 }
 
+extern "C" int tsim_set_object_particles(tsim_ctx *c, int inst, const float *q, int n, float mass, int on_device)
+{
+    int rc = check_ctx(c, inst);
+    if (rc) return rc;
+    Inst &I = c->hinst[inst];
+    if (n < 0 || n > I.objcap || (n > 0 && (!q || !(mass > 0.f) || !std::isfinite(mass))))
+        return fail(TSIM_ERR_INVALID_ARG, "object particles: 0 <= n <= " + std::to_string(I.objcap) +
+                                              ", positions given and mass > 0");
+    if (n > 0) {
+        // xyz rows of 12 bytes into float4 slots of 16
+        CU(cudaMemcpy2DAsync(c->d.objq + I.obj0, sizeof(float4), q, 3 * sizeof(float), 3 * sizeof(float), (size_t)n,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    }
+    I.nobj = n;
+    I.objm = n > 0 ? mass : 0.f;
+    int mx = 0;
+    for (int i = 0; i < c->n_inst; ++i) mx = std::max(mx, c->hinst[i].nobj);
+    if ((mx > 0) != (c->max_nobj > 0) || mx > c->max_nobj) invalidate_graphs(c);
+    c->max_nobj = mx;
+    if (c->have_particles[inst]) c->need_prologue[inst] = 1;
+    rc = upload_inst(c);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(c->stream));      // host arrays may be freed after return
+    return TSIM_OK;
+}
+
 extern "C" int tsim_set_trajectory(tsim_ctx *c, int inst, const tsim_keyframe *kf, int n_kf, int on_device)
 {
     int rc = check_ctx(c, inst);
@@ -424,6 +456,7 @@ static int run_prologue(tsim_ctx *c, int inst)
     int rc = set_dirty(c, inst, 1);
     if (rc) return rc;
     launch_transfer(c->d, MODE_PROLOGUE_, I.block0, I.nblocks, c->stream);
+    launch_object_p2g(c->d, MODE_PROLOGUE_, inst, 1, I.nobj, c->stream);
     CU(cudaGetLastError());
     rc = set_dirty(c, inst, 0);
     if (rc) return rc;
@@ -492,10 +525,12 @@ static int launch_substeps_stream(tsim_ctx *c, int n)
         }
         for (int j = 1; j < limit; ++j) {
             launch_transfer(c->d, MODE_ITER_, 0, (int)c->total_blocks, c->stream);
+            launch_object_p2g(c->d, MODE_ITER_, 0, c->n_inst, c->max_nobj, c->stream);
             launch_grid(c->d, c->max_nodes, c->grid_threads, c->grid_flat, c->stream);
         }
         if (c->profile) CU(cudaEventRecord(e0, c->stream));
         launch_transfer(c->d, MODE_COMMIT_, 0, (int)c->total_blocks, c->stream);
+        launch_object_p2g(c->d, MODE_COMMIT_, 0, c->n_inst, c->max_nobj, c->stream);
         if (c->profile) CU(cudaEventRecord(e1, c->stream));
         CU(cudaGetLastError());
     }
@@ -529,6 +564,7 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
     dim3 grid_grid, grid_blk;
     grid_launch_shape(d, c->max_nodes, c->grid_threads, c->grid_flat, grid_grid, grid_blk);
     const dim3 tr_grid((unsigned int)c->total_blocks), tr_blk(NT), sp_grid(SPILL_CTAS);
+    const dim3 obj_grid((unsigned int)((c->max_nobj + 255) / 256), (unsigned int)c->n_inst);
     cudaGraphNode_t prev = nullptr;
     out.n = n;
     for (auto e : out.ev) cudaEventDestroy(e);
@@ -541,6 +577,7 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
         void *a_spill[] = {&d};
         void *a_grid[] = {&d, &h, &use1};
         void *a_tr[] = {&d, &zero};
+        void *a_obj[] = {&d, &zero};
         cudaGraphNode_t n_r0, n_chk, n_while, n_ev0 = nullptr, n_commit, n_ev1;
         rc = add_kernel(g, &n_r0, prev ? &prev : nullptr, prev ? 1 : 0, fn_round_begin(),
                         dim3(round_begin_ctas(d)), dim3(256), a_r0);
@@ -569,31 +606,43 @@ static int build_chunk(tsim_ctx *c, int n, GraphChunk &out)
         }
         CU(cudaGraphAddNode(&n_while, g, while_deps, nullptr, n_while_deps, &wp));
         cudaGraph_t body = wp.conditional.phGraph_out[0];
-        cudaGraphNode_t b_tr[2], b_chk;
+        cudaGraphNode_t b_tr[3], b_chk;
+        int n_tr = 2;
         // the transfer of the cell blocks and of the spill slots run side by side
         rc = add_kernel(body, &b_tr[0], nullptr, 0, fn_transfer(MODE_ITER_), tr_grid, tr_blk, a_tr,
                         transfer_smem_bytes());
         if (rc) break;
         rc = add_kernel(body, &b_tr[1], nullptr, 0, fn_spill(MODE_ITER_), sp_grid, tr_blk, a_spill);
         if (rc) break;
-        rc = add_kernel(body, &b_chk, b_tr, 2, fn_grid(c->grid_flat), grid_grid, grid_blk, a_grid);
+        if (c->max_nobj > 0) {           // the particle-represented indenter, a third parallel branch
+            rc = add_kernel(body, &b_tr[2], nullptr, 0, fn_object_p2g(MODE_ITER_), obj_grid, dim3(256), a_obj);
+            if (rc) break;
+            n_tr = 3;
+        }
+        rc = add_kernel(body, &b_chk, b_tr, n_tr, fn_grid(c->grid_flat), grid_grid, grid_blk, a_grid);
         if (rc) break;
         cudaGraphNode_t last = n_while;
         if (c->profile) {
             CU(cudaGraphAddEventRecordNode(&n_ev0, g, &last, 1, e0));
             last = n_ev0;
         }
-        cudaGraphNode_t n_commits[2];
+        cudaGraphNode_t n_commits[3];
+        int n_cm = 2;
         rc = add_kernel(g, &n_commits[0], &last, 1, fn_transfer(MODE_COMMIT_), tr_grid, tr_blk, a_tr,
                         transfer_smem_bytes());
         if (rc) break;
         rc = add_kernel(g, &n_commits[1], &last, 1, fn_spill(MODE_COMMIT_), sp_grid, tr_blk, a_spill);
         if (rc) break;
+        if (c->max_nobj > 0) {
+            rc = add_kernel(g, &n_commits[2], &last, 1, fn_object_p2g(MODE_COMMIT_), obj_grid, dim3(256), a_obj);
+            if (rc) break;
+            n_cm = 3;
+        }
         if (c->profile) {
-            CU(cudaGraphAddEventRecordNode(&n_ev1, g, n_commits, 2, out.ev.back()));
+            CU(cudaGraphAddEventRecordNode(&n_ev1, g, n_commits, n_cm, out.ev.back()));
             prev = n_ev1;
         } else {
-            CU(cudaGraphAddEmptyNode(&n_commit, g, n_commits, 2));
+            CU(cudaGraphAddEmptyNode(&n_commit, g, n_commits, n_cm));
             prev = n_commit;
         }
     }

@@ -56,6 +56,11 @@ struct Inst {                      // per-instance constants
     int nkf;
     int spc;                       // spill slots of this instance (particles beyond a full cell block)
     long long sp0;                 // first spill slot
+    // particle-represented indenter (the paper's coupling): nobj > 0 particles
+    // objq[obj0 ..] in the indenter frame, each of mass objm; no SDF contact then
+    long long obj0;
+    int nobj, objcap;
+    float objm;
 };
 
 struct Pose {
@@ -97,6 +102,7 @@ struct Dev {                       // device pointers (passed by value to kernel
     float4 *acc, *vel;
     int *blk_inst;
     unsigned short *sortc;         // per cell block, the cell sort of its first repeat pass in a substep
+    float4 *objq;                  // object particles of all instances (indenter frame, xyz)
     Inst *inst;
     InstState *ist;
     Global *G;

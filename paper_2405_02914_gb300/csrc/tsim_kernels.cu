@@ -107,7 +107,7 @@ __device__ __forceinline__ void grid_velocity(const Dev &d, const Inst &I, const
     V[0] = a.y / a.x + I.dt * I.g[0];
     V[1] = a.z / a.x + I.dt * I.g[1];
     V[2] = a.w / a.x + I.dt * I.g[2];
-    if (I.ind_kind != K_NONE) {
+    if (I.ind_kind != K_NONE && I.nobj == 0) {         // object particles replace the SDF contact
         const Pose &P = S->pose;
         float xw[3] = {(ax - I.ox) * I.dx, (ay - I.oy) * I.dx, (az - I.oz) * I.dx};
         float n[3];
@@ -1075,6 +1075,64 @@ static_assert(offsetof(TransferSmem, idx) % 16 == 0 && (CAP * 2) % 16 == 0 && (2
                   (SORTC * 2) % 16 == 0,
               "bulk copies of the stored cell sort: 16-byte aligned, 16-byte multiples");
 
+// ---------------------------------------------------------------- object particles
+
+// P2G (Eqs. 1-3, no stress term) of the particle-represented indenter of
+// instance inst0 + blockIdx.y, one thread per object particle: rigid, at the
+// indenter pose of the state that enters this P2G (substep k for a repeat
+// pass, k + 1 for a commit, the next substep for a prologue), each with the
+// prescribed velocity v_lin + omega z x (x - c) and the affine field of that
+// motion, C = omega [[0,-1,0],[1,0,0],[0,0,0]]; global vector atomics.
+// Nodes outside the node box receive nothing.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_object_p2g(Dev d, int inst0)
+{
+    const int inst = inst0 + blockIdx.y;
+    const Inst &I = d.inst[inst];
+    if ((long long)blockIdx.x * blockDim.x >= I.nobj) return;
+    const InstState *S = d.ist + inst;
+    if (MODE == MODE_PROLOGUE) {
+        if (!S->dirty) return;
+    } else {
+        const int ph = S->phase;
+        if (MODE == MODE_ITER && ph != 0) return;
+        if (MODE == MODE_COMMIT && ph != 1) return;
+    }
+    __shared__ Pose sp;
+    if (threadIdx.x == 0) {
+        if (MODE == MODE_ITER) sp = S->pose;
+        else pose_eval(I, d.kf + (long long)inst * MAX_KF * 5, MODE == MODE_COMMIT ? d.G->k_cur + 1 : d.G->k_next, sp);
+    }
+    __syncthreads();
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= I.nobj) return;
+    const float4 ql = d.objq[I.obj0 + q];
+    const float xw[3] = {sp.c[0] + sp.cs * ql.x - sp.sn * ql.y, sp.c[1] + sp.sn * ql.x + sp.cs * ql.y, sp.c[2] + ql.z};
+    float vo[3];
+    object_velocity(sp, xw, vo);
+    int base[3];
+    float f[3], w[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) bspline(xw[a], I.inv_dx, base[a], f[a], w[a]);
+    const float m = I.objm, om = sp.omega * I.dx;     // C d with d in cells: omega dx (-d_y, d_x, 0)
+    for (int i = 0; i < 3; ++i) {
+        const int ax = base[0] + i + I.ox;
+        if (ax < 0 || ax >= I.nx) continue;
+        for (int j = 0; j < 3; ++j) {
+            const int ay = base[1] + j + I.oy;
+            if (ay < 0 || ay >= I.ny) continue;
+            const float dxc = (float)i - f[0], dyc = (float)j - f[1];
+            const float u0 = vo[0] - om * dyc, u1 = vo[1] + om * dxc;
+            for (int k = 0; k < 3; ++k) {
+                const int az = base[2] + k + I.oz;
+                if (az < 0 || az >= I.nz) continue;
+                const float wm = w[0][i] * w[1][j] * w[2][k] * m;
+                atomicAdd(&d.acc[node_of(I, ax, ay, az)], make_float4(wm, wm * u0, wm * u1, wm * vo[2]));
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- staging <-> slots
 
 __global__ void k_bin_staged(Dev d, int inst, int par)
@@ -1355,6 +1413,21 @@ cudaError_t setup_kernels()
 }
 
 int block_slots() { return CAP; }
+
+void launch_object_p2g(const Dev &d, int mode, int inst0, int rows, int max_obj, cudaStream_t s)
+{
+    if (max_obj <= 0 || rows <= 0) return;
+    const dim3 g(cdiv(max_obj, 256), rows);
+    if (mode == MODE_PROLOGUE) k_object_p2g<MODE_PROLOGUE><<<g, 256, 0, s>>>(d, inst0);
+    else if (mode == MODE_ITER) k_object_p2g<MODE_ITER><<<g, 256, 0, s>>>(d, inst0);
+    else k_object_p2g<MODE_COMMIT><<<g, 256, 0, s>>>(d, inst0);
+}
+
+void *fn_object_p2g(int mode)
+{
+    return mode == MODE_PROLOGUE ? (void *)k_object_p2g<MODE_PROLOGUE>
+                                 : mode == MODE_ITER ? (void *)k_object_p2g<MODE_ITER> : (void *)k_object_p2g<MODE_COMMIT>;
+}
 
 void launch_transfer(const Dev &d, int mode, int block_offset, int nblocks, cudaStream_t s)
 {

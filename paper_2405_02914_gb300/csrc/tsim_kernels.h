@@ -13,6 +13,8 @@ void launch_set_end(const Dev &d, long long n, cudaStream_t s);
 void grid_launch_shape(const Dev &d, long long max_nodes, int threads, int flat, dim3 &grid, dim3 &block);
 void launch_grid(const Dev &d, long long max_nodes, int threads, int flat, cudaStream_t s);
 void launch_transfer(const Dev &d, int mode, int block_offset, int nblocks, cudaStream_t s);
+void launch_object_p2g(const Dev &d, int mode, int inst0, int rows, int max_obj, cudaStream_t s);
+void *fn_object_p2g(int mode);
 void launch_bin_staged(const Dev &d, int inst, int n, int par, cudaStream_t s);
 void launch_gather(const Dev &d, int inst, long long positions, int par, cudaStream_t s);
 void launch_pick(const Dev &d, int inst, const int *ids, int m, float *out, cudaStream_t s);

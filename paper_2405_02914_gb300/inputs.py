@@ -25,7 +25,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Sequence
+from typing import List, Optional, Sequence
 
 import numpy as np
 
@@ -102,6 +102,8 @@ class Indenter:
     tip_offset: float
     perm: np.ndarray = dataclasses.field(default_factory=lambda: np.arange(256, dtype=np.int32))
     mu_k: float = 0.0
+    obj: Optional[np.ndarray] = None      # object particles (indenter frame), or None: SDF contact
+    obj_m: float = 0.0                    # mass of one object particle
 
     def params8(self) -> np.ndarray:
         p = np.zeros(8, dtype=np.float64)
@@ -132,6 +134,46 @@ def perlin_plate(hx: float, hy: float, hz: float, rnd: float, amp: float,
     perm = np.random.Generator(np.random.Philox(key=seed + 0x5EED)).permutation(256).astype(np.int32)
     return Indenter(PERLIN, [hx, hy, hz, rnd, amp, period, persistence, float(octaves)],
                     mu, hz, perm)
+
+
+def object_particles(ind: Indenter, spacing: float) -> np.ndarray:
+    """Points of a lattice of the given spacing (cell centres, symmetric about
+    the indenter frame's centre) inside the solid indenter, in the indenter
+    frame: sphere, cylinder (flat faces horizontal) and box, with their edge
+    rounding.  The object of the particle-represented indenter."""
+    p = ind.params
+    if ind.kind == SPHERE:
+        ext = np.array([p[0]] * 3)
+    elif ind.kind == CYLINDER:
+        ext = np.array([p[0], p[0], p[1] / 2])
+    elif ind.kind == BOX:
+        ext = np.array(p[:3], dtype=np.float64)
+    else:
+        raise ValueError("object particles for sphere, cylinder and box indenters")
+    axes = [(np.arange(-int(np.ceil(e / spacing)), int(np.ceil(e / spacing))) + 0.5) * spacing for e in ext]
+    q = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+    if ind.kind == SPHERE:
+        inside = np.linalg.norm(q, axis=1) <= p[0]
+    elif ind.kind == CYLINDER:
+        r, rnd = p[0], p[2]
+        d = np.stack([np.hypot(q[:, 0], q[:, 1]) - (r - rnd), np.abs(q[:, 2]) - (p[1] / 2 - rnd)], 1)
+        inside = np.linalg.norm(np.maximum(d, 0.0), axis=1) <= rnd
+    else:
+        rnd = p[3]
+        d = np.abs(q) - (ext - rnd)
+        inside = np.linalg.norm(np.maximum(d, 0.0), axis=1) <= rnd
+    return q[inside].astype(np.float32)
+
+
+def with_object_particles(scene: "Scene", per_cell: int = 8) -> "Scene":
+    """The scene with its indenter represented by particles (the paper's own
+    coupling): per_cell (8) particles per grid cell at the gel's density, so
+    each carries the mass of an elastomer particle."""
+    spacing = scene.gel.dx / round(per_cell ** (1.0 / 3.0))
+    ind = dataclasses.replace(scene.ind)
+    ind.obj = object_particles(ind, spacing)
+    ind.obj_m = float(scene.mat.rho * spacing ** 3)
+    return dataclasses.replace(scene, ind=ind, name=scene.name + "+objparticles")
 
 
 def no_indenter() -> Indenter:

@@ -25,7 +25,7 @@ EXPORTS = ["tsim_create", "tsim_set_solver", "tsim_set_indenter", "tsim_set_traj
            "tsim_read_grid", "tsim_read_surface", "tsim_read_markers", "tsim_read_log", "tsim_sync",
            "tsim_stats", "tsim_use_graph", "tsim_profile", "tsim_kernel_time", "tsim_pass_time", "tsim_last_error",
            "tsim_block_slots", "tsim_destroy", "tsim_p2g_noalloc", "tsim_read_displacement", "tsim_read_indenter_height",
-           "tsim_set_tuning", "tsim_get_tuning", "tsim_autotune"]
+           "tsim_set_tuning", "tsim_get_tuning", "tsim_autotune", "tsim_set_object_particles"]
 
 
 class TsimError(RuntimeError):
@@ -111,6 +111,7 @@ def load():
             "tsim_p2g_noalloc": (C.c_int, [P(GelDesc), P(MaterialDesc), C.c_float, vp, vp, vp, vp, C.c_int,
                                            vp, vp]),
             "tsim_set_tuning": (C.c_int, [vp, P(Tuning)]),
+            "tsim_set_object_particles": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_float, C.c_int]),
             "tsim_get_tuning": (C.c_int, [vp, P(Tuning)]),
             "tsim_autotune": (C.c_int, [vp, C.c_int, P(Tuning)]),
         }
@@ -226,6 +227,17 @@ def tsim_set_solver(ctx, solver: SolverDesc):
 
 def tsim_set_indenter(ctx, inst, ind: IndenterDesc):
     _check(load().tsim_set_indenter(ctx, inst, C.byref(ind)))
+
+
+def tsim_set_object_particles(ctx, inst, q, mass):
+    """q: (n, 3) object particles in the indenter frame (numpy or CUDA
+    tensor, float32), each of the given mass; n = 0 (or None) returns to the
+    SDF contact."""
+    if q is None or len(q) == 0:
+        _check(load().tsim_set_object_particles(ctx, inst, None, 0, 0.0, 0))
+        return
+    p, on, keep = _ptr(q, np.float32)
+    _check(load().tsim_set_object_particles(ctx, inst, p, int(len(q)), float(mass), on))
 
 
 def tsim_set_trajectory(ctx, inst, kf):
@@ -391,6 +403,8 @@ class Sim:
         tsim_set_solver(self.ctx, solver_desc(scenes[0].solver))
         for i, s in enumerate(scenes):
             tsim_set_indenter(self.ctx, i, indenter_desc(s.ind))
+            if getattr(s.ind, "obj", None) is not None:
+                tsim_set_object_particles(self.ctx, i, s.ind.obj, s.ind.obj_m)
             tsim_set_trajectory(self.ctx, i, s.keyframes)
         for i, s in enumerate(scenes):
             if states is not None and states[i] is not None:

@@ -500,6 +500,63 @@ def test_static_kinetic_friction_projection():
         assert np.abs(vr - want * t_hat).max() < 1e-15
 
 
+def test_object_particle_p2g_transfers_the_rigid_motion_exactly():
+    """Object particles (the paper's particle-represented indenter) carry
+    the rigid velocity v_lin + omega z x (x - c) and its affine field, so
+    their P2G alone gives every node with mass exactly the rigid velocity at
+    the node (APIC transfers affine fields exactly), the total mass n m and
+    the total momentum m sum v.  A wrong sign of C or of the rotation, or a
+    missing affine term, fails this."""
+    dx = 0.5e-3
+    gel = I.Gel(16, 16, 8, dx)
+    # the sphere and its stencils stay inside the node box (z up to 7.5 mm)
+    kf = I.keyframes([(0, 4e-3, 4e-3, 4.4e-3, 0.0), (100, 4.6e-3, 3.7e-3, 4.2e-3, 0.4)])
+    ind = I.sphere(1e-3, 0.5)
+    ind.obj = I.object_particles(ind, dx / 2)
+    ind.obj_m = 2.5e-8
+    sc = I.Scene(gel, I.Material(gravity=(0.0, 0.0, 0.0)), ind, kf, I.Solver(dt=1e-5))
+    s, o = O.make_scene(sc), O.make_indenter(ind)
+    ps = O.pose(kf, 37, 1e-5, ind.tip_offset)
+    assert abs(ps.omega) > 0 and abs(ps.vlin[0]) > 0
+    M, MG = O.object_p2g(s, o, ps)
+    n = len(ind.obj)
+    assert M.sum() == pytest.approx(n * ind.obj_m, rel=1e-12)
+    q = ind.obj.astype(np.float64)
+    xw = np.stack([ps.c[0] + ps.cs * q[:, 0] - ps.sn * q[:, 1], ps.c[1] + ps.sn * q[:, 0] + ps.cs * q[:, 1],
+                   ps.c[2] + q[:, 2]], 1)
+    vq = np.stack([ps.vlin[0] - ps.omega * (xw[:, 1] - ps.c[1]), ps.vlin[1] + ps.omega * (xw[:, 0] - ps.c[0]),
+                   np.full(n, ps.vlin[2])], 1)
+    assert np.abs(MG.sum(0) - ind.obj_m * vq.sum(0)).max() < 1e-12 * ind.obj_m * n
+    nx, ny, nz = gel.nodes
+    ox, oy, oz = gel.origin
+    idx = np.nonzero(M > 0)[0]
+    ax, ay, az = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    xn = np.stack([(ax - ox) * dx, (ay - oy) * dx, (az - oz) * dx], 1)
+    vn = np.stack([ps.vlin[0] - ps.omega * (xn[:, 1] - ps.c[1]), ps.vlin[1] + ps.omega * (xn[:, 0] - ps.c[0]),
+                   np.full(idx.size, ps.vlin[2])], 1)
+    assert np.abs(MG[idx] / M[idx, None] - vn).max() < 1e-12
+
+
+def test_object_particles_press_the_gel():
+    """A press with the particle-represented sphere (no SDF contact) pushes
+    the gel top under it down, by an amount comparable to the SDF contact
+    press of the same trajectory, and a pure press still takes one pass per
+    substep."""
+    sc = I.scene_small(cx=12, cy=12, cz=4, n_press=60, mu=0.6, press=0.4e-3)
+    out = {}
+    for mode, scn in (("sdf", sc), ("particles", I.with_object_particles(sc))):
+        s, o = O.make_scene(scn), O.make_indenter(scn.ind)
+        st = _state(scn)
+        z0 = st.x[:, 2].copy()
+        p, _ = O.run(s, o, scn.keyframes, 0, 60, st)
+        assert np.all(p == 1)
+        tip = scn.keyframes[1, 1:3]
+        r = np.hypot(st.x[:, 0] - tip[0], st.x[:, 1] - tip[1])
+        top = z0 > z0.max() - scn.gel.dx
+        out[mode] = (z0 - st.x[:, 2])[top & (r < scn.gel.dx)].mean()
+    assert out["particles"] > 0.3 * out["sdf"] > 0, out
+
+
 def test_pose_interpolation():
     kf = I.keyframes([(0, 0.01, 0.01, 0.005, 0.0), (100, 0.01, 0.01, 0.004, 0.0),
                       (300, 0.013, 0.01, 0.004, 0.0), (500, 0.013, 0.01, 0.004, 0.6)])
