@@ -149,10 +149,60 @@ def _oracle_sample(scene, threads, max_seconds):
     return x.shape[0] * passes / el, done, passes, el, x.shape[0]
 
 
-def cpu_baseline(scene, max_seconds=12.0):
+RENDER_SPP, RENDER_BOUNCES = 128, 4
+
+
+def render_setup(height, scene):
+    """LEDs, albedo and description of the sensor image of a readout."""
+    from paper_2405_02914_gb300 import inputs as I
+    H, W = height.shape
+    pitch = scene.readout_pitch
+    leds = I.sensor_leds(W, H, pitch, scene.gel.height, "gelsight")
+    return leds, I.base_texture(W, H, seed=1), pitch
+
+
+def render_leg(height, scene, stream, reps=5):
+    """The sensor image (path tracing, 128 samples per pixel, 4 reflections)
+    of the last frame's surface, CUDA events around each render."""
+    import torch
+    from paper_2405_02914_gb300 import tsim as T
+    leds, alb, pitch = render_setup(height, scene)
+    H, W = height.shape
+    d = T.render_desc(leds, RENDER_SPP, RENDER_BOUNCES, 0.0, 1)
+    ta = torch.from_numpy(alb).to(height.device)
+    out = torch.empty((H, W, 3), device=height.device)
+    T.tsim_render(height, ta, pitch, d, out, stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    ev[0].record(stream)
+    for r in range(reps):
+        T.tsim_render(height, ta, pitch, d, out, stream)
+        ev[r + 1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[-1]) / reps
+    paths = W * H * RENDER_SPP
+    return {"ms_per_frame": ms, "paths_per_s": paths / (ms * 1e-3), "frames_per_s": 1e3 / ms,
+            "pixels": [W, H], "spp": RENDER_SPP, "max_bounces": RENDER_BOUNCES, "leds": "4 (red, green, blue, white)",
+            "bound": "alu", "mean_rgb": [float(v) for v in out.mean(dim=(0, 1)).cpu()]}
+
+
+def cpu_baseline(scene, max_seconds=12.0, height=None):
     """The FP64 oracle as it stands on the host cores: all cores (the record)
-    and one core (nested), each on the first substeps of the same scene."""
+    and one core (nested), each on the first substeps of the same scene; with
+    a height field also the oracle's sensor image of it (one core)."""
     import oracle as O
+    render = None
+    if height is not None:
+        import numpy as np
+        from oracle import render_oracle as RO
+        leds, alb, pitch = render_setup(height, scene)
+        spp = 8
+        t0 = time.perf_counter()
+        RO.render(np.asarray(height, dtype=np.float64), alb.astype(np.float64), pitch,
+                  RO.make_desc(leds, spp, RENDER_BOUNCES, 0.0, 1))
+        el = time.perf_counter() - t0
+        paths = height.shape[0] * height.shape[1] * spp
+        render = {"paths_per_s": paths / el, "cores": 1, "kind": "oracle",
+                  "sample": "the same frame at %d samples per pixel (%d paths), FP64, %.2f s" % (spp, paths, el)}
     cores = O.threads()
     v1, d1, p1, e1, n = _oracle_sample(scene, 1, max_seconds)
     out1 = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -160,12 +210,17 @@ def cpu_baseline(scene, max_seconds=12.0):
                       "%.1f s" % (d1, p1, n, e1)}
     if cores <= 1:
         out1["nproc"] = os.cpu_count()
+        if render:
+            out1["render"] = render
         return out1
     va, da, pa, ea, _ = _oracle_sample(scene, cores, max_seconds)
-    return {"value": va, "unit": UNIT, "cores": cores, "kind": "oracle", "nproc": os.cpu_count(),
-            "sample": "first %d substeps (%d passes) of the %d-particle scene from rest, FP64 oracle, all-cores "
-                      "variant (%d threads, private grids summed in thread order), %.1f s" % (da, pa, n, cores, ea),
-            "single_thread": out1}
+    out = {"value": va, "unit": UNIT, "cores": cores, "kind": "oracle", "nproc": os.cpu_count(),
+           "sample": "first %d substeps (%d passes) of the %d-particle scene from rest, FP64 oracle, all-cores "
+                     "variant (%d threads, private grids summed in thread order), %.1f s" % (da, pa, n, cores, ea),
+           "single_thread": out1}
+    if render:
+        out["render"] = render
+    return out
 
 
 def aggregate_ranks(ms, e2e_s, updates, e2e_updates, world, device):
@@ -380,6 +435,9 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate vs IMPM frames/s leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched record")
+    ap.add_argument("--no-render", action="store_true", help="skip the sensor-image (path tracing) leg")
+    ap.add_argument("--render-only", action="store_true",
+                    help="profiling aid: only the sensor image of a synthetic 128 x 128 pressed membrane")
     ap.add_argument("--autotune", type=int, default=600,
                     help="substeps of online launch-configuration tuning before the timed region (0: off)")
     ap.add_argument("--no-graph", action="store_true",
@@ -412,6 +470,16 @@ def main():
         return run_reference(args, scene)
     if args.save_state or args.load_state:
         return profile_state(args, scene)
+    if args.render_only:
+        import numpy as np
+        import torch
+        n, p = scene.readout_px, scene.readout_pitch
+        y, x = np.mgrid[0:n, 0:n]
+        r2 = (((x + 0.5) - n / 2) ** 2 + ((y + 0.5) - n / 2) ** 2) * p ** 2
+        h = scene.gel.height - 1e-3 * np.exp(-r2 / (2 * 3e-3 ** 2))         # a 1 mm press of a 3 mm radius
+        frame = torch.from_numpy(np.ascontiguousarray(h, dtype=np.float32)).to("cuda:0")
+        print(json.dumps({"render": render_leg(frame, scene, torch.cuda.current_stream())}), flush=True)
+        return
 
     import numpy as np
     import torch
@@ -624,8 +692,14 @@ def main():
             line["surrogate"] = surrogate_leg()
         except Exception as e:          # reported, never silently replaced by another path
             line["surrogate"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    frame = outs[0][0]
+    if not args.no_render and world == 1:
+        try:
+            line["render"] = render_leg(frame, scene, stream)
+        except Exception as e:          # reported, never silently replaced by another path
+            line["render"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(scene)
+        line["cpu_baseline"] = cpu_baseline(scene, height=None if args.no_render else frame.cpu().numpy())
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -338,6 +338,50 @@ int tsim_kernel_time(tsim_ctx *ctx, int64_t *launches, double *total_ms);
 int tsim_p2g_noalloc(const tsim_gel_desc *gel, const tsim_material *mat, float dt, const float *x,
                      const float *v, const float *C, const float *F, int n, float *grid, void *stream);
 
+/* ---- sensor image (Sec. III-B path tracing, Sec. IV image metrics) ---- */
+
+#define TSIM_MAX_LEDS 4
+
+/* Path-tracing setup (all lengths in metres, the sensor frame of the
+ * readout: pixel (i, j) at ((j + 0.5) pitch, (i + 0.5) pitch)).  LED k is the
+ * rectangle c[k] + a u[k] + b v[k], |a|, |b| <= 1, emitting RGB radiance
+ * L[k] on the side of u[k] x v[k]; the plane z = z_floor below the surface
+ * absorbs (the camera window).  spp samples per pixel (the paper uses 128),
+ * at most max_bounces (1..32) reflections per path; seed selects the
+ * random numbers (SplitMix64 of a per-sample counter). */
+typedef struct {
+    float c[TSIM_MAX_LEDS][3];
+    float u[TSIM_MAX_LEDS][3];
+    float v[TSIM_MAX_LEDS][3];
+    float L[TSIM_MAX_LEDS][3];
+    int n_lights;
+    int spp;
+    int max_bounces;
+    float z_floor;
+    uint64_t seed;
+} tsim_render_desc;
+
+/* Sensor image of a membrane height field (Sec. III-B, Sec. IV-B): an
+ * orthographic camera below the gel sees the Lambertian membrane (maximum
+ * roughness) z = height(x, y) lit by the LEDs; each sample is a reverse
+ * path of diffuse reflections (cosine-weighted, attenuated by the albedo at
+ * each reflection) that adds what reaches an LED.  height: H x W (e.g. from
+ * tsim_read_surface), albedo: H x W x 3 (the base texture), rgb: H x W x 3
+ * out, the mean over spp samples.  All three are device arrays (4-byte
+ * aligned; TSIM_ERR_INVALID_ARG otherwise).  Asynchronous on stream; calls
+ * share a small static device scratch and must not overlap. */
+int tsim_render(const float *height, const float *albedo, int W, int H, float pitch,
+                const tsim_render_desc *desc, float *rgb, void *stream);
+
+/* Image similarity of two H x W x C device images with values in
+ * [0, max_value] (Sec. IV): out[0] = MSE over all values, out[1] = PSNR =
+ * 10 log10(max_value^2 / MSE) (infinite for equal images), out[2] = mean
+ * SSIM (Wang et al. 2004: 11 x 11 Gaussian window of sigma 1.5 inside the
+ * image, K1 = 0.01, K2 = 0.03, averaged over windows and channels).  out is
+ * a host array of 3; the call waits for its work on stream.  W, H >= 11. */
+int tsim_image_metrics(const float *a, const float *b, int W, int H, int C, float max_value, double *out,
+                       void *stream);
+
 /* Reason for the last failure on this thread (never NULL). */
 const char *tsim_last_error(void);
 

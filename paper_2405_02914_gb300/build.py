@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtsim.so")
-UNITS = ["tsim_kernels.cu", "tsim_api.cu", "tsim_noalloc.cu", "tsurr.cu"]
+UNITS = ["tsim_kernels.cu", "tsim_api.cu", "tsim_noalloc.cu", "tsurr.cu", "tsim_render.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-Xptxas", "-v"]

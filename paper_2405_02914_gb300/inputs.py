@@ -176,6 +176,37 @@ def with_object_particles(scene: "Scene", per_cell: int = 8) -> "Scene":
     return dataclasses.replace(scene, ind=ind, name=scene.name + "+objparticles")
 
 
+def sensor_leds(W: int, H: int, pitch: float, gel_height: float, colors: str = "gelsight"):
+    """Four LED panels on the side faces of the gel under a W x H readout of
+    the given pitch, each spanning its face and 5-95 % of the gel's height
+    (inside the gel: no panel edge at the membrane's height, where a path's
+    first step would meet it edge-on) and emitting inward (the emitting
+    side of u x v): (centre, u, v, rgb) tuples.  colors: "gelsight" (red, green, blue, white radiance 1) or
+    "white" (all four white, as in the slip and rotation sensor)."""
+    X, Y, Z = W * pitch, H * pitch, gel_height
+    rgb = ([(1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0), (1.0, 1.0, 1.0)] if colors == "gelsight"
+           else [(1.0, 1.0, 1.0)] * 4)
+    hz = (0.0, 0.0, 0.45 * Z)
+    return [((0.0, Y / 2, Z / 2), (0.0, Y / 2, 0.0), hz, rgb[0]),          # x = 0, emits +x
+            ((X, Y / 2, Z / 2), (0.0, -Y / 2, 0.0), hz, rgb[1]),           # x = X, emits -x
+            ((X / 2, 0.0, Z / 2), (-X / 2, 0.0, 0.0), hz, rgb[2]),         # y = 0, emits +y
+            ((X / 2, Y, Z / 2), (X / 2, 0.0, 0.0), hz, rgb[3])]            # y = Y, emits -y
+
+
+def base_texture(W: int, H: int, seed: int = 0) -> np.ndarray:
+    """Synthetic (H, W, 3) albedo in [0.55, 0.85] (the real sensors' base
+    images are not available): smooth seeded blotches."""
+    rng = np.random.Generator(np.random.Philox(key=seed + 0x7E47))
+    a = rng.uniform(0.0, 1.0, (H // 8 + 2, W // 8 + 2, 3))
+    yy = np.clip((np.arange(H) + 0.5) / 8.0, 0, a.shape[0] - 1.001)
+    xx = np.clip((np.arange(W) + 0.5) / 8.0, 0, a.shape[1] - 1.001)
+    i0, j0 = yy.astype(int), xx.astype(int)
+    fy, fx = (yy - i0)[:, None, None], (xx - j0)[None, :, None]
+    t = ((1 - fy) * ((1 - fx) * a[i0][:, j0] + fx * a[i0][:, j0 + 1]) +
+         fy * ((1 - fx) * a[i0 + 1][:, j0] + fx * a[i0 + 1][:, j0 + 1]))
+    return np.ascontiguousarray(0.55 + 0.3 * t, dtype=np.float32)
+
+
 def no_indenter() -> Indenter:
     return Indenter(NONE, [], 0.0, 0.0)
 

@@ -25,7 +25,8 @@ EXPORTS = ["tsim_create", "tsim_set_solver", "tsim_set_indenter", "tsim_set_traj
            "tsim_read_grid", "tsim_read_surface", "tsim_read_markers", "tsim_read_log", "tsim_sync",
            "tsim_stats", "tsim_use_graph", "tsim_profile", "tsim_kernel_time", "tsim_pass_time", "tsim_last_error",
            "tsim_block_slots", "tsim_destroy", "tsim_p2g_noalloc", "tsim_read_displacement", "tsim_read_indenter_height",
-           "tsim_set_tuning", "tsim_get_tuning", "tsim_autotune", "tsim_set_object_particles"]
+           "tsim_set_tuning", "tsim_get_tuning", "tsim_autotune", "tsim_set_object_particles", "tsim_render",
+           "tsim_image_metrics"]
 
 
 class TsimError(RuntimeError):
@@ -62,6 +63,27 @@ class Stats(C.Structure):
     _fields_ = [("substeps", C.c_int64), ("passes", C.c_int64), ("particle_updates", C.c_int64),
                 ("status", C.c_uint32), ("n_inst", C.c_int32), ("spilled", C.c_int64), ("spill_max", C.c_int32),
                 ("pad_", C.c_int32)]
+
+
+MAX_LEDS = 4
+
+
+class RenderDesc(C.Structure):
+    _fields_ = [("c", (C.c_float * 3) * MAX_LEDS), ("u", (C.c_float * 3) * MAX_LEDS),
+                ("v", (C.c_float * 3) * MAX_LEDS), ("L", (C.c_float * 3) * MAX_LEDS),
+                ("n_lights", C.c_int), ("spp", C.c_int), ("max_bounces", C.c_int), ("z_floor", C.c_float),
+                ("seed", C.c_uint64)]
+
+
+def render_desc(leds, spp=128, max_bounces=4, z_floor=0.0, seed=0) -> RenderDesc:
+    """leds: up to four (centre, u, v, rgb) tuples (see inputs.sensor_leds)."""
+    d = RenderDesc()
+    d.n_lights = len(leds)
+    for k, (c, u, v, L) in enumerate(leds):
+        for a in range(3):
+            d.c[k][a], d.u[k][a], d.v[k][a], d.L[k][a] = c[a], u[a], v[a], L[a]
+    d.spp, d.max_bounces, d.z_floor, d.seed = int(spp), int(max_bounces), float(z_floor), int(seed)
+    return d
 
 
 class Tuning(C.Structure):
@@ -112,6 +134,8 @@ def load():
                                            vp, vp]),
             "tsim_set_tuning": (C.c_int, [vp, P(Tuning)]),
             "tsim_set_object_particles": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_float, C.c_int]),
+            "tsim_render": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_float, P(RenderDesc), vp, vp]),
+            "tsim_image_metrics": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_float, P(C.c_double), vp]),
             "tsim_get_tuning": (C.c_int, [vp, P(Tuning)]),
             "tsim_autotune": (C.c_int, [vp, C.c_int, P(Tuning)]),
         }
@@ -227,6 +251,36 @@ def tsim_set_solver(ctx, solver: SolverDesc):
 
 def tsim_set_indenter(ctx, inst, ind: IndenterDesc):
     _check(load().tsim_set_indenter(ctx, inst, C.byref(ind)))
+
+
+def tsim_render(height, albedo, pitch, desc: RenderDesc, out=None, stream=None):
+    """(H, W, 3) sensor image of the (H, W) height field (CUDA tensors)."""
+    import torch
+    H, W = height.shape
+    for t in (height, albedo) + ((out,) if out is not None else ()):
+        if not t.is_contiguous() or t.dtype != torch.float32:
+            raise ValueError("height, albedo and out must be contiguous float32 tensors")
+    if tuple(albedo.shape) != (H, W, 3):
+        raise ValueError("albedo must be (H, W, 3)")
+    if out is None:
+        out = torch.empty((H, W, 3), dtype=torch.float32, device=height.device)
+    _check(load().tsim_render(C.c_void_p(height.data_ptr()), C.c_void_p(albedo.data_ptr()), int(W), int(H),
+                              float(pitch), C.byref(desc), C.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out
+
+
+def tsim_image_metrics(a, b, max_value=1.0, stream=None):
+    """(MSE, PSNR, SSIM) of two (H, W, C) or (H, W) CUDA tensors."""
+    import torch
+    H, W = a.shape[:2]
+    Cc = a.shape[2] if a.dim() == 3 else 1
+    if not (a.is_contiguous() and b.is_contiguous()) or a.shape != b.shape or a.dtype != torch.float32 or \
+            b.dtype != torch.float32:
+        raise ValueError("a and b must be contiguous float32 tensors of one shape")
+    out = (C.c_double * 3)()
+    _check(load().tsim_image_metrics(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), int(W), int(H), int(Cc),
+                                     float(max_value), out, _stream_handle(stream)))
+    return out[0], out[1], out[2]
 
 
 def tsim_set_object_particles(ctx, inst, q, mass):

@@ -47,13 +47,15 @@ def test_struct_layouts_match_header(tmp_path):
                     'sizeof(tsim_material), sizeof(tsim_indenter_desc), sizeof(tsim_keyframe),'
                     'sizeof(tsim_solver_desc), sizeof(tsim_stats_t), offsetof(tsim_indenter_desc, perm));'
                     'printf("%zu %zu\\n", sizeof(tsim_tuning_t), offsetof(tsim_tuning_t, us_per_mupdate));'
+                    'printf("%zu %zu\\n", sizeof(tsim_render_desc), offsetof(tsim_render_desc, seed));'
                     'return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
     got = [int(a) for a in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [C.sizeof(tsim.GelDesc), C.sizeof(tsim.MaterialDesc), C.sizeof(tsim.IndenterDesc),
             C.sizeof(tsim.Keyframe), C.sizeof(tsim.SolverDesc), C.sizeof(tsim.Stats),
-            tsim.IndenterDesc.perm.offset, C.sizeof(tsim.Tuning), tsim.Tuning.us_per_mupdate.offset]
+            tsim.IndenterDesc.perm.offset, C.sizeof(tsim.Tuning), tsim.Tuning.us_per_mupdate.offset,
+            C.sizeof(tsim.RenderDesc), tsim.RenderDesc.seed.offset]
     assert got == want
 
 
