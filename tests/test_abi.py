@@ -81,6 +81,14 @@ def test_invalid_arguments_rejected_without_gpu():
     L.tsim_destroy(None)
     # the block capacity: 1.25x the 512 particles of a full block at 8 per cell
     assert tsim.tsim_block_slots() == 640
+    # object particles, sensor image and metrics: bad arguments are refused before any GPU work
+    assert L.tsim_set_object_particles(None, 0, None, 0, C.c_float(0.0), 0) == 1
+    assert L.tsim_render(None, None, 8, 8, C.c_float(1e-3), None, None, None) == 1
+    d = tsim.render_desc([], spp=0, max_bounces=1)
+    assert L.tsim_render(None, None, 8, 8, C.c_float(1e-3), C.byref(d), None, None) == 1
+    out = (C.c_double * 3)()
+    assert L.tsim_image_metrics(None, None, 10, 10, 3, C.c_float(1.0), out, None) == 1      # below 11 x 11
+    assert "11 x 11" in L.tsim_last_error().decode()
 
 
 def test_descriptors_from_inputs():
