@@ -91,3 +91,35 @@ def test_surrogate_batch_shapes_and_mask():
     assert set(np.unique(m)) <= {0.0, 1.0} and 0.5 < m.mean() < 0.95
     p = I.surrogate_params(4)
     assert p.size == sum(co * 9 * ci + co for ci, co in I.SURR_CONVS)
+
+
+def test_object_particles_fill_the_shapes():
+    """Lattice points of spacing s inside each shape: the count approaches
+    the volume / s^3, every point is inside, and the set is symmetric about
+    the indenter frame's centre."""
+    import math
+    s = 0.1e-3
+    sph = I.object_particles(I.sphere(1e-3, 0.5), s)
+    assert abs(len(sph) * s ** 3 / (4 / 3 * math.pi * 1e-9) - 1) < 0.03
+    assert np.all(np.linalg.norm(sph, axis=1) <= 1e-3 + 1e-12)
+    assert np.allclose(np.sort(sph[:, 0]), np.sort(-sph[:, 0]), atol=1e-9)
+    bx = I.object_particles(I.box(1e-3, 0.5e-3, 0.5e-3, 0.0, 0.5), s)
+    assert len(bx) == 20 * 10 * 10
+    cy = I.object_particles(I.cylinder(1e-3, 2e-3, 0.0, 0.5), s)
+    assert abs(len(cy) * s ** 3 / (math.pi * 1e-6 * 2e-3) - 1) < 0.03
+    sc = I.with_object_particles(I.scene_small())
+    dx = sc.gel.dx
+    assert sc.ind.obj_m == pytest.approx(sc.mat.rho * dx ** 3 / 8, rel=1e-12)      # an elastomer particle's mass
+
+
+def test_sensor_leds_face_inward_and_texture_is_contiguous():
+    W, H, p, Z = 16, 12, 0.5e-3, 4e-3
+    leds = I.sensor_leds(W, H, p, Z)
+    centre = np.array([W * p / 2, H * p / 2, Z / 2])
+    for c, u, v, rgb in leds:
+        e = np.cross(u, v)
+        assert (centre - np.array(c)) @ e > 0                  # emits toward the gel
+        assert 0 < c[2] - abs(v[2]) and c[2] + abs(v[2]) < Z   # inside the gel's height
+    t = I.base_texture(W, H, seed=3)
+    assert t.shape == (H, W, 3) and t.dtype == np.float32 and t.flags["C_CONTIGUOUS"]
+    assert t.min() >= 0.55 and t.max() <= 0.85
