@@ -5,7 +5,9 @@
   ``every`` substeps, the indenter heightmap (tsim_read_indenter_height) and
   the surface displacement field (tsim_read_displacement) on a 128 x 128
   pixel window at dx/2 pitch, plus the pose and material scalars of the
-  frame.  The frames stay on the device.
+  frame.  The frames stay on the device.  ``generate_chunks`` writes them
+  to disk one batch of trajectories per file and resumes an interrupted
+  run at the first missing chunk; ``load_chunks`` reads them back.
 * ``features``: the network input of a set of frames, x[B,H,W,12] =
   [heightmap, pixel x, pixel y, press depth, slip x, slip y, rotation,
   E, nu, mu, press rate, tangential rate] (lengths in mm, scalars
@@ -29,6 +31,7 @@ from __future__ import annotations
 import dataclasses
 import json
 import math
+import os
 import re
 import time
 
@@ -134,15 +137,17 @@ def _run_chunk(chunk, every, px, pitch, x_ref):
     return H, U, secs, st.passes / max(1, st.substeps) / len(chunk)
 
 
-def generate(scenes, every: int = 100, batch: int = 64, log=None, retries: int = 3) -> Frames:
+def generate(scenes, every: int = 100, batch: int = 64, log=None, retries: int = 3, traj0: int = 0,
+             device: str = "cuda") -> Frames:
     """IMPM frames of ``scenes`` (all on the same pad), ``batch`` trajectories
     per context.  A trajectory whose simulation latches an error (the message
-    names its instance) is left out and the rest of its batch is run again."""
+    names its instance) is left out and the rest of its batch is run again.
+    Trajectory indices start at traj0."""
     torch = _torch()
     px = scenes[0].readout_px
     pitch = scenes[0].readout_pitch
     gel = scenes[0].gel
-    x_ref = torch.from_numpy(np.ascontiguousarray(I.gel_particles(gel)[0])).cuda()
+    x_ref = torch.from_numpy(np.ascontiguousarray(I.gel_particles(gel)[0])).to(device)
     hs, ss, us, pr, tr, sk = [], [], [], [], [], []
     mpm_s, mpm_frames, dropped = 0.0, 0, []
     for c0 in range(0, len(scenes), batch):
@@ -169,16 +174,56 @@ def generate(scenes, every: int = 100, batch: int = 64, log=None, retries: int =
                 k = (f + 1) * every
                 ss.append(frame_scalars(scenes[j], k))
                 pr.append(scenes[j].meta.get("press", 0.0) / MM)
-                tr.append(j)
+                tr.append(traj0 + j)
                 sk.append(k)
         hs.append((H / MM).reshape(-1, px, px))
         us.append((U / MM).reshape(-1, px, px, 3))
         if log:
             log("generated %d/%d trajectories, %.1f s of IMPM, %.2f passes per instance-substep"
                 % (ids[-1] + 1, len(scenes), mpm_s, passes))
-    out = Frames(torch.cat(hs), torch.from_numpy(np.stack(ss)).cuda(), torch.cat(us), np.array(pr, np.float64),
+    out = Frames(torch.cat(hs), torch.from_numpy(np.stack(ss)).to(device), torch.cat(us), np.array(pr, np.float64),
                  np.array(tr), np.array(sk), mpm_s, mpm_frames)
-    out.dropped = dropped
+    out.dropped = [traj0 + j for j in dropped]
+    return out
+
+
+def generate_chunks(scenes, out_dir: str, every: int = 100, batch: int = 64, log=None, retries: int = 3,
+                    device: str = "cuda"):
+    """The frames of ``scenes`` written to out_dir as one file per batch of
+    trajectories (chunk_00000.npz, ...; written to a temporary name, then
+    renamed).  A chunk already on disk is kept, so an interrupted run resumes
+    at the first missing chunk.  Returns the chunk paths."""
+    os.makedirs(out_dir, exist_ok=True)
+    paths = []
+    for ci, c0 in enumerate(range(0, len(scenes), batch)):
+        path = os.path.join(out_dir, "chunk_%05d.npz" % ci)
+        paths.append(path)
+        if os.path.exists(path):
+            if log:
+                log("chunk %d on disk, kept" % ci)
+            continue
+        fr = generate(scenes[c0:c0 + batch], every, batch, log, retries, traj0=c0, device=device)
+        tmp = path + ".part.npz"
+        np.savez(tmp, height=fr.height.cpu().numpy(), scalars=fr.scalars.cpu().numpy(), disp=fr.disp.cpu().numpy(),
+                 press=fr.press, traj=fr.traj, substep=fr.substep, mpm_seconds=fr.mpm_seconds,
+                 mpm_frames=fr.mpm_frames, dropped=np.array(fr.dropped, dtype=np.int64))
+        os.replace(tmp, path)
+    return paths
+
+
+def load_chunks(out_dir: str, device: str = "cuda") -> Frames:
+    """The frames of every chunk file in out_dir, in chunk order, on the device."""
+    torch = _torch()
+    files = sorted(f for f in os.listdir(out_dir) if f.startswith("chunk_") and f.endswith(".npz")
+                   and not f.endswith(".part.npz"))
+    zs = [np.load(os.path.join(out_dir, f)) for f in files]
+    out = Frames(torch.from_numpy(np.concatenate([z["height"] for z in zs])).to(device),
+                 torch.from_numpy(np.concatenate([z["scalars"] for z in zs])).to(device),
+                 torch.from_numpy(np.concatenate([z["disp"] for z in zs])).to(device),
+                 np.concatenate([z["press"] for z in zs]), np.concatenate([z["traj"] for z in zs]),
+                 np.concatenate([z["substep"] for z in zs]), float(sum(float(z["mpm_seconds"]) for z in zs)),
+                 int(sum(int(z["mpm_frames"]) for z in zs)))
+    out.dropped = [int(j) for z in zs for j in z["dropped"]]
     return out
 
 

@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import sys
 import time
 
@@ -35,6 +36,9 @@ def main(argv=None):
     ap.add_argument("--out", required=True)
     ap.add_argument("--report", required=True)
     ap.add_argument("--diag", default=None)
+    ap.add_argument("--cache", default=None,
+                    help="write the frames to this directory, one file per batch of trajectories, and resume "
+                         "from the chunks already there")
     a = ap.parse_args(argv)
 
     def log(msg):
@@ -43,8 +47,14 @@ def main(argv=None):
     t0 = time.time()
     train_sc = I.surrogate_scenes(a.train, seed=0)
     test_sc = I.surrogate_scenes(a.test, seed=1)
-    train_fr = G.generate(train_sc, every=a.every, log=log)
-    test_fr = G.generate(test_sc, every=a.every, log=log)
+    if a.cache:
+        for name, sc in (("train", train_sc), ("test", test_sc)):
+            G.generate_chunks(sc, os.path.join(a.cache, name), every=a.every, log=log)
+        train_fr = G.load_chunks(os.path.join(a.cache, "train"))
+        test_fr = G.load_chunks(os.path.join(a.cache, "test"))
+    else:
+        train_fr = G.generate(train_sc, every=a.every, log=log)
+        test_fr = G.generate(test_sc, every=a.every, log=log)
     log("frames: %d training, %d held-out" % (len(train_fr), len(test_fr)))
     sigma = G.fit_foil(train_fr.subset(np.arange(0, len(train_fr), 7)))
     foil_err = G.frame_errors(G.foil(test_fr, sigma), test_fr)

@@ -94,3 +94,48 @@ def test_forward_flops_counts_real_channels():
     real channels and 622,592 with the 16-wide stored input and output."""
     assert G.forward_flops(8) == 18 * 589824
     assert G.forward_flops(8, stored=True) == 18 * 622592
+
+
+def test_chunked_generation_resumes_and_keeps_trajectory_indices(tmp_path, monkeypatch):
+    """generate_chunks writes one file per batch of trajectories, keeps the
+    chunks already on disk (an interrupted run resumes), numbers the
+    trajectories globally (also the ones left out after a latched error),
+    and load_chunks returns the frames in order.  The IMPM of a batch is
+    replaced here by a stub that encodes the trajectory in its frames."""
+    import numpy as np
+    from paper_2405_02914_gb300 import inputs as I
+    from paper_2405_02914_gb300 import surrogate as G
+    from paper_2405_02914_gb300 import tsim as T
+    torch = pytest.importorskip("torch")
+    scenes = I.surrogate_scenes(5, seed=0)
+    every = scenes[0].n_substeps // 4
+    px = scenes[0].readout_px
+    calls = []
+
+    def stub(chunk, every_, px_, pitch, x_ref):
+        ids = [scenes.index(s) for s in chunk]
+        calls.append(ids)
+        if 3 in ids and len(ids) == 2:             # the first try of trajectory 3's batch latches an error
+            raise T.TsimError(4, "non-finite state (instance %d)" % ids.index(3))
+        nf = chunk[0].n_substeps // every_
+        H = torch.stack([torch.full((nf, px_, px_), float(j)) for j in ids])
+        U = torch.stack([torch.full((nf, px_, px_, 3), float(j) + 0.5) for j in ids])
+        return H, U, 0.25 * len(ids), 1.0
+
+    monkeypatch.setattr(G, "_run_chunk", stub)
+    monkeypatch.setattr(G, "_torch", lambda: torch)     # host logic only: no device needed here
+    paths = G.generate_chunks(scenes, str(tmp_path), every=every, batch=2, device="cpu")
+    assert [p.split("/")[-1] for p in paths] == ["chunk_00000.npz", "chunk_00001.npz", "chunk_00002.npz"]
+    assert calls == [[0, 1], [2, 3], [2], [4]]
+    calls.clear()
+    G.generate_chunks(scenes, str(tmp_path), every=every, batch=2, device="cpu")
+    assert calls == []                                   # everything on disk is kept
+    (tmp_path / "chunk_00002.npz").unlink()
+    G.generate_chunks(scenes, str(tmp_path), every=every, batch=2, device="cpu")
+    assert calls == [[4]]                                # only the missing chunk is simulated again
+    fr = G.load_chunks(str(tmp_path), device="cpu")
+    assert fr.dropped == [3]
+    assert list(fr.traj) == [0] * 4 + [1] * 4 + [2] * 4 + [4] * 4
+    assert np.array_equal(fr.height[:, 0, 0].numpy() * G.MM, fr.traj.astype(np.float32))
+    assert fr.mpm_seconds == pytest.approx(0.25 * 4) and fr.mpm_frames == 16
+    assert list(fr.substep[:4]) == [every, 2 * every, 3 * every, 4 * every]
