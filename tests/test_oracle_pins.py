@@ -716,6 +716,23 @@ def test_all_cores_oracle_equals_serial(threads):
         assert np.linalg.norm(u - w) <= 1e-12 * np.linalg.norm(u)
 
 
+def test_all_cores_oracle_equals_serial_with_object_particles():
+    """The same with the particle-represented indenter, whose P2G the
+    all-cores variant adds after summing the private grids."""
+    sc = I.with_object_particles(I.scene_small(cx=12, cy=12, cz=4, n_press=20, slip=0.3e-3, n_slip=20, mu=0.6,
+                                               press=0.4e-3))
+    s = O.make_scene(sc)
+    ind = O.make_indenter(sc.ind)
+    a = _state(sc)
+    b = a.copy()
+    pa, ea = O.run(s, ind, sc.keyframes, 0, 40, a)
+    pb, eb = O.run_par(s, ind, sc.keyframes, 0, 40, b, 4)
+    assert np.array_equal(pa, pb) and np.array_equal(ea, eb)
+    for u, w in ((a.x, b.x), (a.v, b.v), (a.F, b.F)):
+        assert np.linalg.norm(u - w) <= 1e-12 * np.linalg.norm(u)
+    assert (_state(sc).x[:, 2] - a.x[:, 2]).max() > 0.1 * sc.gel.dx          # it pressed
+
+
 def test_frictionless_sphere_rotation_invariance():
     """A frictionless sphere spinning about its vertical axis exerts no
     tangential force (plain MPM): the surface field is unchanged."""
