@@ -8,7 +8,11 @@
  * follow the paper's statement of the problem: initialise the elastomer and
  * its material (Sec. IV-B), set the object and the pose sequence it moves
  * along (Fig. 2 (A)-(B)), step, and read back the deformed surface that the
- * renderer consumes (Sec. IV-B, Fig. 2 (C)).
+ * renderer consumes (Sec. IV-B, Fig. 2 (C)).  The object is an analytic SDF
+ * with stick/slip contact, or rigid particles taking part in P2G (the
+ * paper's own coupling, tsim_set_object_particles).  Context-free calls
+ * render the sensor image of a surface (Sec. III-B path tracing,
+ * tsim_render) and compare images (Sec. IV, tsim_image_metrics).
  *
  * Conventions
  *   - Every call returns an int status (TSIM_OK or a TSIM_ERR_* code) except
